@@ -1,0 +1,298 @@
+"""Pins for the CPU oracle (no GPU): the paper's worked example, brute force,
+closed forms, a library SVD and the binary128 mode.
+
+Each pin is chosen so that a plausible slip in the oracle (a dropped Lambda, a
+transposed gate index, a wrong sign in the complex rotation, a mis-ordered
+reshape, a wrong truncation rule) fails at least one test here.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.statevector import StateVector
+from paper_1111_3124_gb300 import circuits as C
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def run_both(n, layers, chi_max=1 << 20, cutoff=0.0, prec=oracle.FP64):
+    mps = oracle.OracleMPS(n, chi_max, cutoff, prec)
+    sv = StateVector(n)
+    for layer in layers:
+        for site, U in layer:
+            k = {2: 1, 4: 2, 8: 3}[U.shape[0]]
+            mps.apply_gate(site, U)
+            sv.apply(list(range(site, site + k)), U)
+    return mps, sv
+
+
+def mps_vector(mps, n):
+    out = np.zeros(1 << n, dtype=np.complex128)
+    for x in range(1 << n):
+        bits = [(x >> (n - 1 - q)) & 1 for q in range(n)]
+        out[x] = mps.amplitude(bits)
+    return out
+
+
+# ---------------------------------------------------------- worked example ---
+
+def test_worked_example_sec32():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "worked_example_rdo.txt")) if l.strip() and not l.startswith("#")]
+    m = oracle.OracleMPS(3, 8, 1e-14)
+    init = m.reduced_density([0, 1, 2])
+    exp_init = np.zeros((8, 8))
+    for lab, nq, x, y, v in rows:
+        if lab == "initial":
+            exp_init[int(x, 2), int(y, 2)] = float(v)
+    np.testing.assert_allclose(init, exp_init, atol=5e-8)
+    m.apply_gate(0, C.H)
+    m.apply_gate_on([0, 2], C.CNOT)
+    rho = m.reduced_density([0, 2])
+    exp = np.zeros((4, 4))
+    for lab, nq, x, y, v in rows:
+        if lab == "final":
+            exp[int(x, 2), int(y, 2)] = float(v)
+    # printed to 8 digits
+    np.testing.assert_allclose(rho, exp, atol=5e-8)
+    # the control is the first argument: CNOT(2 -> 0) would leave |00><10| terms
+    assert abs(rho[0, 2]) < 1e-15
+
+
+# ------------------------------------------------------------- dense SVD ---
+
+@pytest.mark.parametrize("m,n", [(1, 1), (5, 3), (3, 5), (16, 16), (33, 17), (8, 40)])
+def test_svd_against_lapack_and_identities(m, n):
+    rng = np.random.default_rng(m * 100 + n)
+    T = rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))
+    sigma, X, Y, sw = oracle.svd(T)
+    assert sw > 0
+    ref = np.linalg.svd(T, compute_uv=False)
+    np.testing.assert_allclose(np.sort(sigma)[::-1], ref, rtol=0, atol=1e-13 * ref[0])
+    np.testing.assert_allclose(X @ np.diag(sigma) @ Y.conj().T, T, atol=1e-13 * ref[0])
+    r = min(m, n)
+    np.testing.assert_allclose(X.conj().T @ X, np.eye(r), atol=1e-13)
+    np.testing.assert_allclose(Y.conj().T @ Y, np.eye(r), atol=1e-13)
+
+
+def test_svd_graded_spectrum_relative_accuracy():
+    """Jacobi's hallmark: tiny singular values of a graded matrix are found to
+    high relative accuracy (Demmel & Veselic 1992), which the Gram route would lose."""
+    rng = np.random.default_rng(7)
+    n = 24
+    q1, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    s_true = np.logspace(0, -12, n)
+    T = (q1 * s_true[None, :])  # columns scaled: T = Q diag(s), singular values s exactly up to rounding
+    sigma, X, Y, _ = oracle.svd(T)
+    np.testing.assert_allclose(np.sort(sigma)[::-1], s_true, rtol=1e-12)
+
+
+def test_svd_binary128_closer_than_fp64():
+    rng = np.random.default_rng(3)
+    T = rng.standard_normal((12, 9)) + 1j * rng.standard_normal((12, 9))
+    s64, *_ = oracle.svd(T, oracle.FP64)
+    s128, X, Y, _ = oracle.svd(T, oracle.BINARY128)
+    np.testing.assert_allclose(np.sort(s64), np.sort(s128), rtol=1e-14)
+    # binary128 reconstruction is exact to the binary64 rounding of the outputs
+    np.testing.assert_allclose(X @ np.diag(s128) @ Y.conj().T, T, atol=1e-15)
+
+
+def test_svd_rank_deficient_and_zero():
+    T = np.zeros((6, 4), dtype=np.complex128)
+    s, X, Y, _ = oracle.svd(T)
+    assert np.all(s == 0)
+    u = np.arange(6) + 1j
+    v = np.arange(4) - 2j
+    s, X, Y, _ = oracle.svd(np.outer(u, v))
+    ss = np.sort(s)[::-1]
+    assert abs(ss[0] - np.linalg.norm(u) * np.linalg.norm(v)) < 1e-12 * ss[0]
+    assert np.all(ss[1:] < 1e-13 * ss[0])
+
+
+# ----------------------------------------------- MPS vs brute-force vector ---
+
+def random_layers(n, depth, rng, ks=(1, 2, 3)):
+    layers = []
+    for _ in range(depth):
+        layer, s = [], int(rng.integers(0, 2))
+        while s < n:
+            k = int(rng.choice(ks))
+            if s + k > n:
+                k = 1
+            layer.append((s, C.haar_unitary(1 << k, rng)))
+            s += k + int(rng.integers(0, 2))
+        layers.append(layer)
+    return layers
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_mps_matches_statevector_mixed_gates(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = 7
+    mps, sv = run_both(n, random_layers(n, 6, rng))
+    np.testing.assert_allclose(mps_vector(mps, n), sv.vector(), atol=1e-13)
+
+
+def test_config1_all_amplitudes_no_truncation():
+    c = C.CONFIGS[1]
+    layers = C.config_circuit(1)
+    mps = oracle.OracleMPS(c["n"], c["chi_max"], c["cutoff"])
+    sv = StateVector(c["n"])
+    for layer in layers:
+        for site, U in layer:
+            k = {2: 1, 4: 2, 8: 3}[U.shape[0]]
+            mps.apply_gate(site, U)
+            sv.apply(list(range(site, site + k)), U)
+            if k >= 2:
+                d = mps.last_diag()
+                assert d["status"] == 0 and d["discarded"] < 1e-26
+    assert C.count_updates(layers) == 45
+    v = mps_vector(mps, c["n"])
+    np.testing.assert_allclose(v, sv.vector(), atol=1e-13)
+    assert abs(np.linalg.norm(v) - 1) < 1e-13
+
+
+def test_schmidt_vectors_are_schmidt_coefficients_eq2():
+    rng = np.random.default_rng(11)
+    n = 8
+    mps, sv = run_both(n, random_layers(n, 5, rng, ks=(2,)))
+    for b in range(n - 1):
+        lam = mps.schmidt(b)
+        ref = sv.schmidt(b)
+        ref = ref[ref > 1e-14]
+        assert len(lam) >= len(ref)
+        np.testing.assert_allclose(np.sort(lam)[::-1][:len(ref)], ref, atol=1e-13)
+        assert abs(np.sum(lam ** 2) - 1) < 1e-13
+
+
+def test_expectation_and_rdo_vs_statevector():
+    rng = np.random.default_rng(5)
+    n = 6
+    mps, sv = run_both(n, random_layers(n, 5, rng))
+    for site, k in [(0, 1), (2, 2), (3, 3), (5, 1)]:
+        O = rng.standard_normal((1 << k, 1 << k)) + 1j * rng.standard_normal((1 << k, 1 << k))
+        O = O + O.conj().T
+        ref = sv.expectation(list(range(site, site + k)), O)
+        assert abs(mps.expectation(site, O) - ref) < 1e-12
+    for qs in ([0], [4, 1], [0, 2, 5], [5, 3, 1, 0]):
+        np.testing.assert_allclose(mps.reduced_density(qs), sv.reduced_density(qs), atol=1e-13)
+
+
+def test_binary128_mode_matches_and_is_tighter():
+    rng = np.random.default_rng(9)
+    n = 6
+    layers = random_layers(n, 5, rng)
+    m64, sv = run_both(n, layers)
+    m128, _ = run_both(n, layers, prec=oracle.BINARY128)
+    v64, v128, vs = mps_vector(m64, n), mps_vector(m128, n), sv.vector()
+    np.testing.assert_allclose(v64, v128, atol=1e-13)
+    # the binary128 run is limited only by the binary64 state vector it is compared to
+    assert np.max(np.abs(v128 - vs)) <= np.max(np.abs(v64 - vs)) + 1e-15
+
+
+# -------------------------------------------------------------- closed forms ---
+
+def test_product_state_rank_one():
+    rng = np.random.default_rng(1)
+    n = 6
+    layers = [[(q, C.haar_unitary(2, rng)) for q in range(n)],
+              [(s, np.kron(C.haar_unitary(2, rng), C.haar_unitary(2, rng))) for s in (0, 2, 4)],
+              [(s, np.kron(C.haar_unitary(2, rng), C.haar_unitary(2, rng))) for s in (1, 3)]]
+    mps, sv = run_both(n, layers, chi_max=64, cutoff=1e-14)
+    for b in range(n - 1):
+        assert mps.bond_dim(b) == 1
+        np.testing.assert_allclose(mps.schmidt(b), [1.0], atol=1e-14)
+    np.testing.assert_allclose(mps_vector(mps, n), sv.vector(), atol=1e-14)
+
+
+def test_bell_and_ghz_spectra():
+    n = 12
+    mps = oracle.OracleMPS(n, 128, 1e-12)
+    for layer in C.ghz_prefix(n):
+        for site, U in layer:
+            mps.apply_gate(site, U)
+    r = 1 / np.sqrt(2)
+    for b in range(n - 1):
+        np.testing.assert_allclose(mps.schmidt(b), [r, r], atol=1e-15)
+    assert abs(mps.amplitude([0] * n) - r) < 1e-15
+    assert abs(mps.amplitude([1] * n) - r) < 1e-15
+    assert abs(mps.amplitude([1] + [0] * (n - 1))) < 1e-15
+
+
+def test_unitarity_of_generated_gates():
+    rng = np.random.default_rng(2)
+    for d in (2, 4, 8):
+        for _ in range(5):
+            U = C.haar_unitary(d, rng)
+            assert np.max(np.abs(U.conj().T @ U - np.eye(d))) < 1e-14
+
+
+# ----------------------------------------------------------------- truncation ---
+
+def _schmidt_gate(a, b):
+    """U(4) whose first column is a|00> + b|11>, completed to a unitary."""
+    M = np.eye(4, dtype=np.complex128)
+    M[:, 0] = [a, 0, 0, b]
+    q, r = np.linalg.qr(M)
+    return q * (np.diag(r) / np.abs(np.diag(r)))[None, :]
+
+
+def test_truncation_to_chi_max_closed_form():
+    U = _schmidt_gate(0.8, 0.6)
+    m = oracle.OracleMPS(2, 1, 0.0)
+    m.apply_gate(0, U)
+    d = m.last_diag()
+    assert d["k"] == 1 and abs(d["discarded"] - 0.36) < 1e-15
+    np.testing.assert_allclose(m.schmidt(0), [1.0], atol=1e-15)
+    assert abs(abs(m.amplitude([0, 0])) - 1) < 1e-14
+    assert abs(m.amplitude([1, 1])) < 1e-15
+
+
+@pytest.mark.parametrize("eps,kept", [(1e-13, 1), (1e-11, 2)])
+def test_truncation_cutoff_rule(eps, kept):
+    U = _schmidt_gate(np.sqrt(1 - eps ** 2), eps)
+    m = oracle.OracleMPS(2, 8, 1e-12)
+    m.apply_gate(0, U)
+    assert m.bond_dim(0) == kept
+    assert abs(np.sum(m.schmidt(0) ** 2) - 1) < 1e-15
+
+
+def test_degenerate_cut_keeps_valid_state():
+    """Bell state cut to chi_max = 1: the two Schmidt values tie; any one branch
+    is a valid truncation. Unique: k = 1, discarded = 1/2, lambda = [1]."""
+    m = oracle.OracleMPS(2, 1, 0.0)
+    m.apply_gate(0, np.kron(C.H, C.I2))
+    m.apply_gate(0, C.CNOT)
+    d = m.last_diag()
+    assert d["k"] == 1 and abs(d["discarded"] - 0.5) < 1e-15
+    a00, a11 = abs(m.amplitude([0, 0])), abs(m.amplitude([1, 1]))
+    assert abs(max(a00, a11) - 1) < 1e-14 and min(a00, a11) < 1e-15
+
+
+def test_single_truncation_fidelity_equals_kept_weight():
+    """From a canonical state, one truncation at one bond loses exactly the
+    discarded weight: |<psi|psi_trunc>|^2 = 1 - w (Schmidt decomposition, Eq. 2),
+    and the kept Schmidt values are the exact top-k, renormalised."""
+    rng = np.random.default_rng(21)
+    n = 8
+    layers = random_layers(n, 6, rng, ks=(2,))
+    exact, sv = run_both(n, layers)
+    b = 3
+    full = exact.schmidt(b)
+    chi_b = len(full)
+    k_cap = max(1, chi_b - 3)
+    U = C.haar_unitary(4, rng)
+    # reference: exact state after the extra gate
+    sv.apply([b, b + 1], U)
+    ref_s = sv.schmidt(b)
+    trunc = oracle.OracleMPS(n, k_cap, 0.0)
+    trunc.set_state(*exact.get_state()[1:])
+    trunc.apply_gate(b, U)
+    d = trunc.last_diag()
+    w = float(np.sum(ref_s[k_cap:] ** 2))
+    assert abs(d["discarded"] - w) < 1e-13
+    np.testing.assert_allclose(trunc.schmidt(b), ref_s[:k_cap] / np.linalg.norm(ref_s[:k_cap]), atol=1e-13)
+    v = mps_vector(trunc, n)
+    f = abs(np.vdot(sv.vector(), v)) ** 2
+    assert abs(f - (1 - w)) < 1e-12
