@@ -1,0 +1,299 @@
+#!/usr/bin/env python
+"""Benchmark: two-site gate updates per second on the n=64, depth-20
+Haar-random U(4) brickwork (+ RZ phases) workload at chi_max = 256.
+
+One step = the whole circuit from |0...0> (630 two-site updates: theta
+formation, Jacobi SVD, truncation, rewrite), inputs resident in HBM.
+Prints one JSON line (rank 0). See the design notes for the roofline
+definitions.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--prec fp64|split]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "two-site gate updates/s at χ=256, mixed-prec vs FP64 on GB300, amp err ≤10^-10".replace(
+    "10^-10", "1e-10")
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 binary64 (no measured figure in MEASURED_PEAKS.json)
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def args_parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--prec", default="fp64", choices=["fp64", "split"])
+    p.add_argument("--cpu-sample", type=int, default=2, help="oracle updates timed for cpu_baseline")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload():
+    from paper_1111_3124_gb300 import circuits as C
+    c = C.CONFIGS[2]
+    layers = C.config_circuit(2)
+    return c, layers, C.count_updates(layers)
+
+
+def grouped(layers):
+    """Each layer -> list of (k, sites, Us) with same-size gates batched."""
+    out = []
+    for layer in layers:
+        by_k = {}
+        for site, U in layer:
+            by_k.setdefault(U.shape[0], []).append((site, U))
+        for d in sorted(by_k):
+            k = {2: 1, 4: 2, 8: 3}[d]
+            gs = by_k[d]
+            out.append((k, np.array([s for s, _ in gs], dtype=np.int32),
+                        np.ascontiguousarray(np.stack([U for _, U in gs]).astype(np.complex128))))
+    return out
+
+
+# ----------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------ CPU oracle ---
+
+def oracle_sample(n_updates: int):
+    """The oracle (as it stands, one host thread) on a bounded sample of the
+    workload: steady-state two-site updates at chi_L = chi = chi_R = 256
+    (theta 512 x 512, truncated to 256) on a synthetic saturated state."""
+    import oracle
+    from paper_1111_3124_gb300 import circuits as C
+    t_total = 0.0
+    for i in range(n_updates):
+        rng = np.random.default_rng(9000 + i)
+        state = C.random_vidal_state(4, (1, 256, 256, 256, 1), rng, decay=2.0)
+        m = oracle.OracleMPS(4, 256, 1e-12)
+        m.set_state(*state)
+        U = C.haar_unitary(4, rng)
+        t0 = time.perf_counter()
+        m.apply_gate(1, U)
+        t_total += time.perf_counter() - t0
+    return n_updates / t_total, t_total
+
+
+def cpu_baseline_obj(n_updates: int):
+    v, t = oracle_sample(n_updates)
+    return {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
+            "sample": "%d steady-state two-site updates at chi=256 (theta 512x512 -> 256) on a synthetic "
+                      "saturated Vidal state, binary64 oracle, one host thread, %.1f s" % (n_updates, t)}
+
+
+# --------------------------------------------------------------- ref arm ---
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    c, layers, nup = workload()
+    for _ in range(a.warmup):
+        oracle_sample(1)
+    times = []
+    for _ in range(a.steps):
+        _, t = oracle_sample(1)
+        times.append(t)
+    v = len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "updates/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": c["name"], "n": c["n"], "depth": c["depth"],
+                                            "chi_max": c["chi_max"], "cutoff": c["cutoff"],
+                                            "step": "one steady-state update (bounded sample)"},
+            "cpu_baseline": {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                             "sample": "one chi=256 update per step on a synthetic saturated state"},
+            "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU arm ---
+
+def run_gpu(a):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_1111_3124_gb300 import build as B
+    if rank == 0:
+        B.build()
+    barrier()
+    B.build()
+    from paper_1111_3124_gb300.mps import MPS, PREC_FP64, PREC_SPLIT
+
+    c, layers, nup = workload()
+    glayers = grouped(layers)
+    dev_layers = [(k, s, torch.from_numpy(U).to("cuda")) for k, s, U in glayers]
+    stream = torch.cuda.Stream()
+    m = MPS(c["n"], c["chi_max"], c["cutoff"], PREC_SPLIT if a.prec == "split" else PREC_FP64)
+    m.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step_device():
+        m.reset()
+        for k, s, dU in dev_layers:
+            m.apply_layer_device(s, dU, k)
+
+    with torch.cuda.stream(stream):
+        for _ in range(a.warmup):
+            step_device()
+        m.sync()
+        chi = m.bond_dims()
+        barrier()
+        # ---- device-resident timed region
+        m.profile(True)
+        times = []
+        with ClockSampler(local) as clk:
+            for _ in range(a.steps):
+                flush.fill_(float(len(times)))  # evict L2 between steps
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                step_device()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+        clocks = clk.summary()
+        prof = {kk: m.profile_read(kk) for kk in range(4)}
+        m.profile(False)
+        # ---- end to end through the public API with host buffers
+        pinned = [(k, s, torch.from_numpy(U).pin_memory().numpy()) for k, s, U in glayers]
+        h2d = int(sum(U.nbytes + s.nbytes for _, s, U in pinned))
+        mid = c["n"] // 2 - 1
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(a.steps):
+            m.reset()
+            for k, s, U in pinned:
+                m.apply_layer(s, U)
+            lam = m.schmidt(mid)
+            d2h = lam.nbytes + 4
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+
+    t_step = sum(times) / len(times) / 1e3
+    t_e2e = e2e_s / a.steps
+    if world > 1:
+        tt = torch.tensor([t_step, t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step, t_e2e = float(tt[0]), float(tt[1])
+    value = nup * world / t_step
+    e2e_value = nup * world / t_e2e
+
+    jac = prof[0]
+    achieved = jac["flops"] / (jac["ms"] / 1e3) / 1e12 if jac["ms"] > 0 else None
+    roof = {"kernel": "k_jacobi_pair (blocked one-sided Jacobi, binary64)", "bound": "alu",
+            "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_NOMINAL_TFLOPS if achieved else None,
+            "peak_source": "nominal GB300 binary64 rate (not in MEASURED_PEAKS.json)",
+            "flops_per_launch": jac["flops"] / max(jac["launches"], 1),
+            "ms_per_launch": jac["ms"] / max(jac["launches"], 1), "traffic": None,
+            "share_of_step": jac["ms"] / (1e3 * t_step * a.steps)}
+    kernels = {name: {"ms_per_step": prof[i]["ms"] / a.steps, "launches_per_step": prof[i]["launches"] / a.steps,
+                      "tflops": prof[i]["flops"] / (prof[i]["ms"] / 1e3) / 1e12 if prof[i]["ms"] > 0 else None}
+               for i, name in enumerate(["jacobi_pair", "theta_contract", "truncate_rewrite", "split_gemm"])}
+    line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Haar U(4) brickwork + RZ)",
+            "config": {"workload": c["name"], "n": c["n"], "depth": c["depth"], "chi_max": c["chi_max"],
+                       "cutoff": c["cutoff"], "updates_per_step": nup, "prec": a.prec,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "256 MiB buffer written between timed steps; working set > L2",
+                       "max_bond": int(max(chi)) if len(chi) else 1},
+            "roofline": roof, "kernels": kernels, "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(prof[0]["launches_all"])}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_obj(a.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    m.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        import oracle
+        oracle.build()
+        run_reference(a)
+        return
+    run_gpu(a)
+
+
+if __name__ == "__main__":
+    main()

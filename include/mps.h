@@ -1,0 +1,209 @@
+/*
+ * mps.h - C ABI of the GB300 (sm_103a) engine for the time-dependent
+ * matrix-product-state (MPS) simulation of quantum circuits.
+ *
+ * Method: A. SaiToh, "A Multiprecision Matrix Calculation Library and Its
+ * Extension Library for a Matrix-Product-State Simulation of Quantum
+ * Computing" (2011), Sec. 3. The state is held in the Vidal form of Eq. (1):
+ * site tensors Gamma_s (the paper's Q_s, 2 x m_{s-1} x m_s complex numbers)
+ * and bond vectors Lambda_s (the paper's V_s, the Schmidt coefficients of the
+ * cut (0..s)|(s+1..n-1), Eq. (2)). A gate on consecutive qubits rewrites only
+ * the tensors it touches (Sec. 3.1); small Schmidt coefficients are truncated.
+ *
+ * Conventions shared by every call:
+ *  - Complex numbers are complex128: two doubles (real, imaginary), interleaved.
+ *  - A k-qubit gate or operator is a 2^k x 2^k row-major complex128 matrix.
+ *    Its row/column index is sum_j b_{site+j} 2^{k-1-j}: the FIRST acted-on
+ *    qubit is the MOST significant bit. (The Sec. 3.2 example, CNOT on qubits
+ *    0 and 2 with 0 as control, fixes this order.)
+ *  - Bond b (0 <= b <= n-2) sits between qubits b and b+1.
+ *  - Host pointers passed in are read before the call returns; the library
+ *    never keeps or frees caller memory. Output buffers are caller-allocated.
+ *  - Every entry point returns an mps_status. Argument errors are reported
+ *    synchronously and leave the state untouched. Errors found on the device
+ *    (for instance a Jacobi SVD that did not converge) are recorded in a
+ *    device status word and reported by the next call that synchronises
+ *    (mps_sync, readouts, exports); the gate that failed leaves its tensors
+ *    unchanged. mps_last_error() returns a message for the calling thread.
+ *  - Calls on one handle are issued on that handle's CUDA stream in order;
+ *    a handle must not be used from two threads at once.
+ */
+#ifndef PAPER_1111_3124_GB300_MPS_H
+#define PAPER_1111_3124_GB300_MPS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mps_state* mps_handle;
+
+typedef enum {
+  MPS_OK = 0,
+  MPS_ERR_ARG = -1,          /* bad argument (null pointer, range, shape)    */
+  MPS_ERR_NOMEM = -2,        /* device or pinned-host allocation failed      */
+  MPS_ERR_CUDA = -3,         /* a CUDA runtime call failed                   */
+  MPS_ERR_NOCONVERGE = -4,   /* Jacobi SVD hit its sweep limit               */
+  MPS_ERR_TIMEOUT = -5,      /* a bounded device wait ran out                */
+  MPS_ERR_NOT_UNITARY = -6,  /* ||U^H U - I||_max > 1e-10                    */
+  MPS_ERR_TOO_LARGE = -7     /* request exceeds a stated size limit          */
+} mps_status;
+
+/* Arithmetic used for the dense contractions of the gate update. */
+typedef enum {
+  MPS_PREC_FP64 = 0,   /* native binary64 on the CUDA cores                   */
+  MPS_PREC_SPLIT = 1   /* binary64-accurate products from sliced bf16 tensor-
+                          core products (Ozaki scheme), binary64 elsewhere    */
+} mps_prec;
+
+/* mps_create - Sec. 3.2 ("mps M(n)"): an n-qubit state |0...0>, i.e.
+ * Gamma_s[0] = [[1]], Gamma_s[1] = [[0]], Lambda_b = [1].
+ *   n        number of qubits, 1 <= n <= 4096
+ *   chi_max  largest bond dimension kept after a gate, 1 <= chi_max <= 1024
+ *            (device memory for the tensors is reserved at this capacity:
+ *            n * 2 * chi_max^2 * 16 bytes)
+ *   cutoff   truncation threshold (Sec. 3.1, "very small coefficients ... are
+ *            truncated out"): after each split, the Schmidt values sigma_j
+ *            with sigma_j <= cutoff * ||sigma||_2 are dropped, at most chi_max
+ *            values are kept (ties broken by column index), at least one, and
+ *            the kept values are renormalised to unit 2-norm. cutoff >= 0.
+ *   out      receives the handle (set to NULL on error).
+ * Errors: MPS_ERR_ARG, MPS_ERR_NOMEM, MPS_ERR_CUDA. */
+int mps_create(int n, int chi_max, double cutoff, mps_handle* out);
+
+/* Releases the handle and all device memory it owns. NULL is accepted. */
+int mps_destroy(mps_handle h);
+
+/* Makes every later call of this handle run on `cuda_stream` (a cudaStream_t
+ * owned by the caller, e.g. a PyTorch stream). NULL restores the handle's own
+ * stream. The caller keeps the stream alive while the handle uses it. */
+int mps_set_stream(mps_handle h, void* cuda_stream);
+
+/* Selects the arithmetic of later gate updates (prec = mps_prec). `slices` is
+ * the number of bf16 slices per operand for MPS_PREC_SPLIT (0 = default 8,
+ * range 3..8); it is ignored for MPS_PREC_FP64. `svd_mode` is reserved and
+ * must be 0 (full Jacobi SVD). */
+int mps_set_mode(mps_handle h, int prec, int slices, int svd_mode);
+
+/* mps_reset - returns the state to |0...0> (same as a fresh mps_create). */
+int mps_reset(mps_handle h);
+
+/* mps_apply_gate - Sec. 3.1 / Sec. 3.2 ("applyU"): applies U in U(2^k),
+ * k in {1,2,3}, to qubits site..site+k-1.
+ *   k = 1: Gamma_site <- u Gamma_site on the physical index (no SVD). Single-
+ *          qubit gates are held back and folded into the next multi-qubit
+ *          gate touching the same qubit, or applied before any readout.
+ *   k = 2: two-site update of Gamma_s, Lambda_s, Gamma_{s+1} (Sec. 3.1):
+ *          theta = Lambda_{s-1} Gamma_s Lambda_s Gamma_{s+1} Lambda_{s+1}
+ *          contracted with U, split by a one-sided Jacobi SVD, truncated
+ *          (see mps_create), outer Lambdas divided back out.
+ *   k = 3: three-site update (U(8) gates are elementary, Sec. 1, Sec. 3.1):
+ *          one theta over three sites split by two successive SVDs.
+ *   U      host pointer, 2^k x 2^k row-major complex128, copied before return.
+ * Errors: MPS_ERR_ARG (k, site range, NULL), MPS_ERR_NOT_UNITARY. */
+int mps_apply_gate(mps_handle h, int site, int k, const double* U);
+
+/* mps_apply_layer - n_gates gates of the same size k on pairwise disjoint
+ * qubit ranges, updated together in one batched pass (the gates of one
+ * circuit layer commute, so the result equals applying them in any order).
+ *   sites  host array of n_gates first sites
+ *   Us     host array of n_gates gates, each 2^k x 2^k complex128, row-major,
+ *          stored one after another
+ * Errors: MPS_ERR_ARG (overlap, range, NULL), MPS_ERR_NOT_UNITARY. */
+int mps_apply_layer(mps_handle h, int k, int n_gates, const int* sites, const double* Us);
+
+/* mps_apply_layer_device - as mps_apply_layer, but the n_gates gates are read
+ * from DEVICE memory (d_Us: n_gates x 2^k x 2^k complex128, row-major, on the
+ * handle's device), so a caller whose gates are already resident in HBM pays
+ * no host-to-device copy. The buffer must stay valid until the handle's stream
+ * has executed this call. No unitarity check is made. Held-back single-qubit
+ * gates on the touched qubits are applied first; k = 1 gates are applied at
+ * once (not held back).
+ *   sites  host array of n_gates first sites (pairwise disjoint ranges)
+ * Errors: MPS_ERR_ARG. */
+int mps_apply_layer_device(mps_handle h, int k, int n_gates, const int* sites, const double* d_Us);
+
+/* mps_amplitude - <bits|psi> = Gamma_0[b_0] Lambda_0 Gamma_1[b_1] ... Gamma_{n-1}[b_{n-1}]
+ * (Eq. 1 evaluated at one basis state).
+ *   bits  host array of n bytes, bits[q] in {0,1} is the value of qubit q
+ *   out   host double[2] (real, imaginary)
+ * Synchronises the stream. */
+int mps_amplitude(mps_handle h, const unsigned char* bits, double* out);
+
+/* mps_amplitudes - `count` amplitudes in one launch; bits is count x n bytes,
+ * out is count x 2 doubles. Synchronises the stream. */
+int mps_amplitudes(mps_handle h, int count, const unsigned char* bits, double* out);
+
+/* mps_expectation - <psi|O|psi> / <psi|psi> for a k-qubit operator O acting on
+ * qubits site..site+k-1 (k in {1,2,3}, same index convention as gates), by a
+ * full transfer-matrix contraction of Eq. (1), exact for the stored tensors.
+ *   out   host double[2]. Synchronises the stream. */
+int mps_expectation(mps_handle h, int site, int k, const double* O, double* out);
+
+/* mps_reduced_density - Sec. 3.2 ("RDO", the tracing-out operation): the
+ * reduced density operator of the listed qubits, normalised to unit trace.
+ *   qubits  host array of nq distinct qubit indices in any order; the first
+ *           listed qubit is the most significant bit of rho's index (as in
+ *           the Sec. 3.2 output |00><11|)
+ *   nq      1 <= nq <= 6
+ *   rho     host buffer of 2^nq x 2^nq complex128, row-major
+ * Errors: MPS_ERR_ARG, MPS_ERR_TOO_LARGE (nq > 6). Synchronises the stream. */
+int mps_reduced_density(mps_handle h, const int* qubits, int nq, double* rho);
+
+/* mps_get_schmidt - copies Lambda_bond (the Schmidt coefficients of the cut
+ * after qubit `bond`, Eq. 2) into lambda (capacity chi_max doubles) and its
+ * length into *len. Synchronises the stream. */
+int mps_get_schmidt(mps_handle h, int bond, double* lambda, int* len);
+
+/* mps_bond_dims - chi[b] = current dimension of bond b, b = 0..n-2 (n-1 ints).
+ * Synchronises the stream. */
+int mps_bond_dims(mps_handle h, int* chi);
+
+/* mps_export - copies the state to host arrays.
+ *   chi      n+1 ints: chi[0] = chi[n] = 1, chi[b+1] = dim of bond b
+ *   gammas   concatenation over s of Gamma_s as [2][chi[s]][chi[s+1]]
+ *            complex128 (may be NULL to query chi only)
+ *   lambdas  concatenation over b = 0..n-2 of Lambda_b (may be NULL)
+ * Synchronises the stream. */
+int mps_export(mps_handle h, int* chi, double* gammas, double* lambdas);
+
+/* mps_import - replaces the state with host arrays laid out as in mps_export.
+ * Every chi entry must lie in [1, chi_max] and chi[0] = chi[n] = 1. */
+int mps_import(mps_handle h, const int* chi, const double* gammas, const double* lambdas);
+
+/* mps_diag - diagnostics of the last gate or layer call, one entry per gate in
+ * call order (at most `cap` entries; *count receives how many exist):
+ *   k[i]          new bond dimension (for k = 3: of the second split)
+ *   discarded[i]  discarded weight sum_{dropped} sigma^2 / sum sigma^2
+ *                 (k = 3: sum over both splits)
+ *   sweeps[i]     Jacobi sweeps used (k = 3: both splits)
+ * Any output pointer may be NULL. Synchronises the stream. */
+int mps_diag(mps_handle h, int cap, int* count, int* k, double* discarded, int* sweeps);
+
+/* Per-kernel-class timing of later calls (not part of the method; used to
+ * measure each kernel against its roofline). enable = 1 brackets every launch
+ * of the classes below with CUDA events on the handle's stream and counts the
+ * executed binary64 flops; enable = 0 stops; each call clears the counters.
+ * Kernel classes: 0 = Jacobi pair rotations, 1 = theta contraction,
+ * 2 = truncation and tensor rewrite (norms, truncate, emit), 3 = split-
+ * precision products. */
+int mps_profile(mps_handle h, int enable);
+
+/* Reads the counters of class `kernel`: summed launch durations in ms, the
+ * number of launches, and the executed flops (binary64 flops for classes 0-2,
+ * tensor-core flops for class 3). `launches_all` (may be NULL) receives the
+ * number of kernels of every class launched since the last mps_profile call.
+ * Synchronises the stream. */
+int mps_profile_read(mps_handle h, int kernel, double* ms, long long* launches, double* flops,
+                     long long* launches_all);
+
+/* mps_sync - waits for the handle's stream and reports a deferred device
+ * error (MPS_ERR_NOCONVERGE, MPS_ERR_TIMEOUT, MPS_ERR_CUDA), clearing it. */
+int mps_sync(mps_handle h);
+
+/* Message describing the last error returned on the calling thread. */
+const char* mps_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAPER_1111_3124_GB300_MPS_H */

@@ -19,15 +19,19 @@
 //   * U(8) gates on three consecutive qubits are elementary gates (Sec. 1, Sec. 3.1):
 //     one theta over three sites, split by two successive SVDs.
 // Readings where the paper is silent (all listed in the design notes):
-//   * truncation keeps sigma_j > cutoff * ||sigma||_2, at most chi_max values,
-//     at least one, then renormalises the kept values to unit 2-norm;
+//   * truncation keeps sigma_j > max(cutoff, m eps) * ||sigma||_2 (m = rows of
+//     the Jacobi working matrix, eps the unit roundoff: values at the SVD's
+//     resolution are numerically zero), at most chi_max values, at least one,
+//     then renormalises the kept values to unit 2-norm;
 //   * ties in sigma are broken by column index (stable descending order);
 //   * the first site a gate acts on is the most significant bit of the gate's
 //     row/column index (fixed by the worked example of Sec. 3.2: CNOT(0,2)
 //     with qubit 0 as control);
 //   * the SVD is the one-sided Hestenes-Jacobi method with cyclic-by-rows
 //     ordering and the complex rotation of Rutishauser / Demmel-Veselic (1992),
-//     stopping when every pair satisfies |a_p^H a_q| <= m*eps*||a_p||*||a_q||.
+//     stopping when every pair satisfies |a_p^H a_q| <= m*eps*||a_p||*||a_q||;
+//     columns with ||a_j|| <= m*eps*||A||_F are numerically zero and are not
+//     rotated (as LAPACK's zgesvj treats negligible columns).
 //
 // Two arithmetic modes share the same templated code: IEEE binary64 and
 // IEEE binary128 (__float128 on x86_64, long double on aarch64).
@@ -101,6 +105,11 @@ int jacobi_columns(int m, int n, std::vector<Cx<R>>& A, std::vector<Cx<R>>& V,
   V.assign((size_t)n * n, Cx<R>());
   for (int j = 0; j < n; ++j) V[(size_t)j * n + j] = Cx<R>(1);
   const R tol = Num<R>::eps() * (R)m;
+  // Columns with ||a_j|| <= m eps ||A||_F are numerically zero (rounding noise
+  // of exact zeros): they take part in no rotation. ||A||_F is invariant.
+  R frob = 0;
+  for (size_t e = 0; e < A.size(); ++e) frob += abs2(A[e]);
+  const R tiny = tol * tol * frob;
   int sweep = 0;
   bool rotated = true;
   while (rotated) {
@@ -118,6 +127,7 @@ int jacobi_columns(int m, int n, std::vector<Cx<R>>& A, std::vector<Cx<R>>& V,
           beta += abs2(aq[r]);
           gamma = gamma + conj(ap[r]) * aq[r];
         }
+        if (!(alpha > tiny) || !(beta > tiny)) continue;
         R g = absc(gamma);
         if (!(g > tol * Num<R>::sqrt_(alpha) * Num<R>::sqrt_(beta))) continue;
         rotated = true;
@@ -198,12 +208,17 @@ struct TruncInfo { int k; double discarded; };
 // Truncation of a spectrum: keep sigma_j > cutoff * ||sigma||, at most chi_max
 // values, at least one; the kept values, renormalised to unit 2-norm, become
 // the new Schmidt vector.
+// Values at or below the SVD's resolution, mw * eps * ||sigma|| (mw = rows of
+// the Jacobi working matrix), count as zero whatever the cutoff.
 template <class R>
 TruncInfo truncate(const std::vector<R>& sigma, const std::vector<int>& ord, int chi_max,
-                   double cutoff, std::vector<R>& lam) {
+                   double cutoff, int mw, std::vector<R>& lam) {
   R total = 0;
   for (R s : sigma) total += s * s;
-  R thr = (R)cutoff * Num<R>::sqrt_(total);
+  R rel = (R)cutoff;
+  const R floor_ = Num<R>::eps() * (R)mw;
+  if (rel < floor_) rel = floor_;
+  R thr = rel * Num<R>::sqrt_(total);
   int k = 0;
   for (int j : ord) if (sigma[j] > thr) ++k;
   if (k > chi_max) k = chi_max;
@@ -316,7 +331,7 @@ class OracleMPS : public OracleBase {
     int sw = svd_general<R>(M, N, th, sigma, X, Y);
     if (sw < 0) { diag_ = Diag{0, 0, 60, -4}; return -4; }
     std::vector<int> ord = order_desc(sigma);
-    TruncInfo ti = truncate<R>(sigma, ord, chi_max, cutoff, newlam);
+    TruncInfo ti = truncate<R>(sigma, ord, chi_max, cutoff, M > N ? M : N, newlam);
     const int kk = ti.k, r = (int)sigma.size();
     // Gamma'_s[i,a,c] = X[(i,a), ord c] / Lambda_{s-1}[a]
     std::vector<Cx<R>> g0((size_t)2 * xl * kk), g1((size_t)2 * kk * xr);
@@ -383,7 +398,7 @@ class OracleMPS : public OracleBase {
     int sw1 = svd_general<R>(M1, N1, th, s1, X1, Y1);
     if (sw1 < 0) { diag_ = Diag{0, 0, 60, -4}; return -4; }
     std::vector<int> o1 = order_desc(s1);
-    TruncInfo t1 = truncate<R>(s1, o1, chi_max, cutoff, lam1);
+    TruncInfo t1 = truncate<R>(s1, o1, chi_max, cutoff, M1 > N1 ? M1 : N1, lam1);
     const int k1 = t1.k;
     // second matrix: R[c,(j,l,b)] = lam1[c] conj(Y1[(j,l,b), o1 c]), reshaped to rows (j,c), cols (l,b)
     const int M2 = 2 * k1, N2 = 2 * xr;
@@ -399,7 +414,7 @@ class OracleMPS : public OracleBase {
     int sw2 = svd_general<R>(M2, N2, th2, s2, X2, Y2);
     if (sw2 < 0) { diag_ = Diag{0, 0, 60, -4}; return -4; }
     std::vector<int> o2 = order_desc(s2);
-    TruncInfo t2 = truncate<R>(s2, o2, chi_max, cutoff, lam2);
+    TruncInfo t2 = truncate<R>(s2, o2, chi_max, cutoff, M2 > N2 ? M2 : N2, lam2);
     const int k2 = t2.k;
     std::vector<Cx<R>> g0((size_t)2 * xl * k1), g1((size_t)2 * k1 * k2), g2((size_t)2 * k2 * xr);
     for (int i = 0; i < 2; ++i)

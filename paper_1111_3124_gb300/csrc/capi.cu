@@ -1,0 +1,858 @@
+// C ABI (include/mps.h) and host orchestration of the gate-update engine.
+//
+// A handle owns the Vidal-form tensors of one MPS in device memory (layout
+// in engine.cuh), a per-gate workspace that grows with the widest layer seen,
+// pinned staging buffers for gates and task tables, and a CUDA stream.
+// Bond dimensions live on the device; the host keeps only upper bounds
+// (ub[b+1] >= chi of bond b, exact for generic gates) to size grids, so a
+// layer's launches need no device-to-host read except the one-int
+// convergence count after each Jacobi sweep.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mps.h"
+#include "engine.cuh"
+#include "kernels.cuh"
+
+using namespace mpsgb;
+typedef std::complex<double> cd;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(e_ == cudaErrorMemoryAllocation ? MPS_ERR_NOMEM : MPS_ERR_CUDA,             \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+  } while (0)
+
+constexpr int kMaxSweeps = 40;
+
+struct Slot {
+  double2* A = nullptr;
+  double2* V = nullptr;
+  double2* T = nullptr;
+  double* sigma = nullptr;
+  int* perm = nullptr;
+};
+
+}  // namespace
+
+struct mps_state {
+  int n = 0, cap = 0;
+  double cutoff = 0.0;
+  int prec = MPS_PREC_FP64, slices = 8, svd_mode = 0;
+  cudaStream_t own = nullptr, stream = nullptr;
+  double2* gamma = nullptr;
+  double* lambda = nullptr;
+  int* chi = nullptr;
+  std::vector<int> ub;                      // n+1 upper bounds of chi
+  std::vector<std::array<cd, 4>> pend;      // held-back single-qubit gates
+  std::vector<char> has_pend;
+  std::vector<Slot> slots;
+  GateTask* d_tasks = nullptr;
+  TaskMeta* d_meta = nullptr;
+  double2* d_gates = nullptr;
+  int task_cap = 0;
+  GateTask* h_tasks = nullptr;               // pinned
+  double2* h_gates = nullptr;                // pinned
+  int* d_counter = nullptr;
+  int* h_counter = nullptr;                  // pinned
+  SiteTask* d_site = nullptr;
+  SiteTask* h_site = nullptr;                // pinned
+  double2* d_site_gates = nullptr;
+  double2* h_site_gates = nullptr;           // pinned
+  int last_ntask = 0;
+  int last_k = 0;
+  // per-kernel-class profiling (mps_profile)
+  int prof = 0;
+  std::vector<cudaEvent_t> evs;
+  size_t ev_next = 0;
+  std::vector<std::array<int, 3>> prof_rec;  // (class, begin event, end event)
+  double prof_flops_host[4] = {0, 0, 0, 0};
+  long long prof_launch[4] = {0, 0, 0, 0};
+  long long launches_all = 0;
+  unsigned long long* d_prof_flops = nullptr;  // device counters, one per class
+};
+
+namespace {
+
+size_t gamma_elems(const mps_state* h) { return (size_t)h->n * 2 * h->cap * h->cap; }
+double2* site_ptr(const mps_state* h, int s) { return h->gamma + (size_t)s * 2 * h->cap * h->cap; }
+double* bond_ptr(const mps_state* h, int b) { return h->lambda + (size_t)(b + 1) * h->cap; }
+
+// Profiling brackets: pbeg records a start event (profiling on) and returns its
+// index; pend records the end event and counts the launches of the class.
+int pbeg(mps_state* h) {
+  if (!h->prof) return -1;
+  if (h->ev_next + 2 > h->evs.size()) {
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      h->evs.push_back(e);
+    }
+  }
+  const int idx = (int)h->ev_next;
+  h->ev_next += 2;
+  cudaEventRecord(h->evs[idx], h->stream);
+  return idx;
+}
+void pend(mps_state* h, int kind, int idx, int nlaunch, double host_flops = 0.0) {
+  h->launches_all += nlaunch;
+  if (idx < 0) return;
+  cudaEventRecord(h->evs[idx + 1], h->stream);
+  h->prof_rec.push_back({kind, idx, idx + 1});
+  h->prof_launch[kind] += nlaunch;
+  h->prof_flops_host[kind] += host_flops;
+}
+
+__global__ void k_reset(double2* gamma, double* lambda, int* chi, int n, int cap) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s <= n; s += gridDim.x * blockDim.x) {
+    if (s < n) {
+      gamma[(size_t)s * 2 * cap * cap] = make_double2(1.0, 0.0);
+      gamma[((size_t)s * 2 + 1) * cap * cap] = make_double2(0.0, 0.0);
+    }
+    lambda[(size_t)s * cap] = 1.0;
+    chi[s] = 1;
+  }
+}
+
+int reset_state(mps_state* h) {
+  k_reset<<<(h->n + 256) / 256, 256, 0, h->stream>>>(h->gamma, h->lambda, h->chi, h->n, h->cap);
+  CK(cudaGetLastError());
+  h->ub.assign(h->n + 1, 1);
+  h->has_pend.assign(h->n, 0);
+  return MPS_OK;
+}
+
+int ensure_tasks(mps_state* h, int ntask) {
+  if (ntask <= h->task_cap) return MPS_OK;
+  int cap = std::max(ntask, 2 * h->task_cap);
+  cudaFree(h->d_tasks); cudaFree(h->d_meta); cudaFree(h->d_gates);
+  cudaFreeHost(h->h_tasks); cudaFreeHost(h->h_gates);
+  h->d_tasks = nullptr; h->d_meta = nullptr; h->d_gates = nullptr; h->h_tasks = nullptr; h->h_gates = nullptr;
+  h->task_cap = 0;
+  CK(cudaMalloc(&h->d_tasks, sizeof(GateTask) * cap));
+  CK(cudaMalloc(&h->d_meta, sizeof(TaskMeta) * cap));
+  CK(cudaMemset(h->d_meta, 0, sizeof(TaskMeta) * cap));
+  CK(cudaMalloc(&h->d_gates, sizeof(double2) * 64 * cap));
+  CK(cudaMallocHost(&h->h_tasks, sizeof(GateTask) * cap));
+  CK(cudaMallocHost(&h->h_gates, sizeof(double2) * 64 * cap));
+  h->task_cap = cap;
+  return MPS_OK;
+}
+
+int ensure_slots(mps_state* h, int nslot) {
+  const size_t c2 = (size_t)h->cap * h->cap;
+  while ((int)h->slots.size() < nslot) {
+    Slot s;
+    CK(cudaMalloc(&s.A, sizeof(double2) * 8 * c2));
+    CK(cudaMalloc(&s.V, sizeof(double2) * 4 * c2));
+    CK(cudaMalloc(&s.T, sizeof(double2) * 4 * c2));
+    CK(cudaMalloc(&s.sigma, sizeof(double) * 2 * h->cap));
+    CK(cudaMalloc(&s.perm, sizeof(int) * 2 * h->cap));
+    h->slots.push_back(s);
+  }
+  return MPS_OK;
+}
+
+void free_state(mps_state* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (Slot& s : h->slots) {
+    cudaFree(s.A); cudaFree(s.V); cudaFree(s.T); cudaFree(s.sigma); cudaFree(s.perm);
+  }
+  cudaFree(h->gamma); cudaFree(h->lambda); cudaFree(h->chi);
+  cudaFree(h->d_tasks); cudaFree(h->d_meta); cudaFree(h->d_gates); cudaFree(h->d_counter);
+  cudaFree(h->d_site); cudaFree(h->d_site_gates);
+  cudaFreeHost(h->h_tasks); cudaFreeHost(h->h_gates); cudaFreeHost(h->h_counter);
+  cudaFreeHost(h->h_site); cudaFreeHost(h->h_site_gates);
+  cudaFree(h->d_prof_flops);
+  for (cudaEvent_t e : h->evs) cudaEventDestroy(e);
+  if (h->own) cudaStreamDestroy(h->own);
+  delete h;
+}
+
+bool is_unitary(const double* U, int d) {
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      cd acc = 0;
+      for (int r = 0; r < d; ++r) acc += std::conj(cd(U[2 * (r * d + i)], U[2 * (r * d + i) + 1])) * cd(U[2 * (r * d + j)], U[2 * (r * d + j) + 1]);
+      if (std::abs(acc - cd(i == j ? 1.0 : 0.0)) > 1e-10) return false;
+    }
+  return true;
+}
+
+// U' = U (P_site (x) ... (x) P_{site+k-1}) with the held-back single-qubit gates.
+void fold_pending(mps_state* h, int site, int k, const double* U, double2* out) {
+  const int d = 1 << k;
+  std::vector<cd> P((size_t)d * d, cd(0));
+  for (int r = 0; r < d; ++r)
+    for (int c = 0; c < d; ++c) {
+      cd v = 1.0;
+      for (int j = 0; j < k; ++j) {
+        const int br = (r >> (k - 1 - j)) & 1, bc = (c >> (k - 1 - j)) & 1;
+        const int q = site + j;
+        if (h->has_pend[q]) v *= h->pend[q][br * 2 + bc];
+        else v *= (br == bc) ? 1.0 : 0.0;
+      }
+      P[(size_t)r * d + c] = v;
+    }
+  for (int r = 0; r < d; ++r)
+    for (int c = 0; c < d; ++c) {
+      cd acc = 0;
+      for (int m = 0; m < d; ++m) acc += cd(U[2 * (r * d + m)], U[2 * (r * d + m) + 1]) * P[(size_t)m * d + c];
+      out[r * d + c] = make_double2(acc.real(), acc.imag());
+    }
+  for (int j = 0; j < k; ++j) h->has_pend[site + j] = 0;
+}
+
+// Applies every held-back single-qubit gate (before readouts and exports).
+int flush_pending(mps_state* h) {
+  int cnt = 0, el_ub = 1;
+  for (int s = 0; s < h->n; ++s) cnt += h->has_pend[s];
+  if (!cnt) return MPS_OK;
+  if (!h->d_site || !h->h_site) {
+    CK(cudaMalloc(&h->d_site, sizeof(SiteTask) * h->n));
+    CK(cudaMalloc(&h->d_site_gates, sizeof(double2) * 4 * h->n));
+    CK(cudaMallocHost(&h->h_site, sizeof(SiteTask) * h->n));
+    CK(cudaMallocHost(&h->h_site_gates, sizeof(double2) * 4 * h->n));
+  }
+  CK(cudaStreamSynchronize(h->stream));  // pinned staging reuse
+  int t = 0;
+  for (int s = 0; s < h->n; ++s) {
+    if (!h->has_pend[s]) continue;
+    for (int e = 0; e < 4; ++e) h->h_site_gates[4 * t + e] = make_double2(h->pend[s][e].real(), h->pend[s][e].imag());
+    SiteTask st;
+    st.g = site_ptr(h, s);
+    st.chi = h->chi;
+    st.site = s;
+    st.cap = h->cap;
+    st.U = h->d_site_gates + 4 * t;
+    h->h_site[t] = st;
+    el_ub = std::max(el_ub, h->ub[s] * h->ub[s + 1]);
+    h->has_pend[s] = 0;
+    ++t;
+  }
+  CK(cudaMemcpyAsync(h->d_site_gates, h->h_site_gates, sizeof(double2) * 4 * t, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d_site, h->h_site, sizeof(SiteTask) * t, cudaMemcpyHostToDevice, h->stream));
+  launch_apply1(h->d_site, t, el_ub, h->stream);
+  h->launches_all += 1;
+  CK(cudaGetLastError());
+  return MPS_OK;
+}
+
+// Blocked one-sided Jacobi on every task's working matrix (A, or T for the
+// second split of a three-site update). One launch per round-robin round;
+// a sweep ends with a convergence count read back to the host.
+int run_svd(mps_state* h, int ntask, int nw_ub, int second) {
+  launch_init_V(h->d_tasks, h->d_meta, ntask, nw_ub, h->stream);
+  h->launches_all += 1;
+  const int nb = (nw_ub + kBlockW - 1) / kBlockW;
+  const int nbe = nb + (nb & 1);
+  unsigned long long* fl = h->prof ? h->d_prof_flops : nullptr;
+  for (int sw = 0; sw < kMaxSweeps; ++sw) {
+    for (int r = 0; r < nbe - 1; ++r) {
+      const int ev = pbeg(h);
+      launch_jacobi_round(h->d_tasks, h->d_meta, ntask, r, nbe / 2, second, fl, h->stream);
+      pend(h, 0, ev, 1);
+    }
+    CK(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
+    launch_sweep_end(h->d_meta, ntask, kMaxSweeps, h->d_counter, h->stream);
+    h->launches_all += 1;
+    CK(cudaMemcpyAsync(h->h_counter, h->d_counter, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (*h->h_counter == 0) break;
+  }
+  CK(cudaGetLastError());
+  return MPS_OK;
+}
+
+int validate_layer(mps_state* h, int k, int ng, const int* sites, const void* Us) {
+  if (k < 1 || k > 3) return fail(MPS_ERR_ARG, "k must be 1, 2 or 3");
+  if (ng < 0 || (ng > 0 && (!sites || !Us))) return fail(MPS_ERR_ARG, "null sites/gates");
+  std::vector<char> used(h->n, 0);
+  for (int g = 0; g < ng; ++g) {
+    if (sites[g] < 0 || sites[g] + k > h->n) return fail(MPS_ERR_ARG, "gate site out of range");
+    for (int j = 0; j < k; ++j) {
+      if (used[sites[g] + j]) return fail(MPS_ERR_ARG, "gates of a layer overlap");
+      used[sites[g] + j] = 1;
+    }
+  }
+  return MPS_OK;
+}
+
+// The update pipeline of one layer of k-site gates (k = 2, 3) whose gate
+// matrices are on the device at d_U + g * u_stride.
+int run_update(mps_state* h, int k, int ng, const int* sites, const double2* d_U, int u_stride) {
+  int xl_ub = 1, x0_ub = 1, xr_ub = 1, nw_ub = 1;
+  double fl_contract = 0.0;
+  for (int g = 0; g < ng; ++g) {
+    const int s = sites[g];
+    GateTask t;
+    std::memset(&t, 0, sizeof(t));
+    t.g0 = site_ptr(h, s);
+    t.g1 = site_ptr(h, s + 1);
+    t.g2 = k == 3 ? site_ptr(h, s + 2) : nullptr;
+    t.lamL = bond_ptr(h, s - 1);
+    t.lam0 = bond_ptr(h, s);
+    t.lam1 = bond_ptr(h, s + 1);
+    t.lamR = bond_ptr(h, s + k - 1);
+    t.chi = h->chi;
+    t.U = d_U + (size_t)u_stride * g;
+    t.site = s;
+    t.k = k;
+    t.cap = h->cap;
+    t.cutoff = h->cutoff;
+    t.A = h->slots[g].A;
+    t.V = h->slots[g].V;
+    t.T = h->slots[g].T;
+    t.sigma = h->slots[g].sigma;
+    t.perm = h->slots[g].perm;
+    h->h_tasks[g] = t;
+    const int xl = h->ub[s], x0 = h->ub[s + 1], xr = h->ub[s + k];
+    xl_ub = std::max(xl_ub, xl);
+    x0_ub = std::max(x0_ub, x0);
+    xr_ub = std::max(xr_ub, xr);
+    nw_ub = std::max(nw_ub, std::min(2 * xl, (k == 3 ? 4 : 2) * xr));
+    if (k == 2) fl_contract += 32.0 * xl * x0 * xr + 128.0 * xl * xr;
+    else fl_contract += 32.0 * x0 * h->ub[s + 2] * xr + 64.0 * xl * x0 * xr + 512.0 * xl * xr;
+  }
+  CK(cudaMemcpyAsync(h->d_tasks, h->h_tasks, sizeof(GateTask) * ng, cudaMemcpyHostToDevice, h->stream));
+  launch_setup(h->d_tasks, h->d_meta, ng, 0, h->stream);
+  h->launches_all += 1;
+  int ev = pbeg(h);
+  if (k == 2) launch_contract2(h->d_tasks, h->d_meta, ng, xl_ub, xr_ub, h->stream);
+  else launch_contract3(h->d_tasks, h->d_meta, ng, x0_ub, xl_ub, xr_ub, h->stream);
+  pend(h, 1, ev, k == 2 ? 1 : 2, fl_contract);
+  launch_frob(h->d_tasks, h->d_meta, ng, (long long)(2 * xl_ub) * ((k == 3 ? 4 : 2) * xr_ub), 0, h->stream);
+  h->launches_all += 1;
+  CK(cudaGetLastError());
+  int rc = run_svd(h, ng, nw_ub, 0);
+  if (rc) return rc;
+  const int k_ub = std::min(h->cap, nw_ub);
+  ev = pbeg(h);
+  launch_colnorms(h->d_tasks, h->d_meta, ng, nw_ub, 0, h->stream);
+  launch_truncate(h->d_tasks, h->d_meta, ng, 0, h->cap, h->stream);
+  if (k == 2) {
+    launch_emit_left(h->d_tasks, h->d_meta, ng, xl_ub, k_ub, 0, h->stream);
+    launch_emit_right(h->d_tasks, h->d_meta, ng, xr_ub, k_ub, 0, h->stream);
+    pend(h, 2, ev, 4);
+    for (int g = 0; g < ng; ++g) {
+      const int s = sites[g];
+      h->ub[s + 1] = std::min(h->cap, std::min(2 * h->ub[s], 2 * h->ub[s + 2]));
+    }
+  } else {
+    launch_emit_left(h->d_tasks, h->d_meta, ng, xl_ub, k_ub, 0, h->stream);
+    launch_form_second(h->d_tasks, h->d_meta, ng, k_ub, xr_ub, h->stream);
+    launch_setup(h->d_tasks, h->d_meta, ng, 1, h->stream);
+    pend(h, 2, ev, 5);
+    int nw2_ub = 1;
+    for (int g = 0; g < ng; ++g) {
+      const int s = sites[g];
+      const int k1 = std::min(h->cap, std::min(2 * h->ub[s], 4 * h->ub[s + 3]));
+      nw2_ub = std::max(nw2_ub, std::min(2 * k1, 2 * h->ub[s + 3]));
+    }
+    launch_frob(h->d_tasks, h->d_meta, ng, (long long)(2 * k_ub) * (2 * xr_ub), 1, h->stream);
+    h->launches_all += 1;
+    rc = run_svd(h, ng, nw2_ub, 1);
+    if (rc) return rc;
+    const int k2_ub = std::min(h->cap, nw2_ub);
+    ev = pbeg(h);
+    launch_colnorms(h->d_tasks, h->d_meta, ng, nw2_ub, 1, h->stream);
+    launch_truncate(h->d_tasks, h->d_meta, ng, 1, h->cap, h->stream);
+    launch_emit_left(h->d_tasks, h->d_meta, ng, k_ub, k2_ub, 1, h->stream);
+    launch_emit_right(h->d_tasks, h->d_meta, ng, xr_ub, k2_ub, 1, h->stream);
+    pend(h, 2, ev, 4);
+    for (int g = 0; g < ng; ++g) {
+      const int s = sites[g];
+      const int k1 = std::min(h->cap, std::min(2 * h->ub[s], 4 * h->ub[s + 3]));
+      h->ub[s + 1] = k1;
+      h->ub[s + 2] = std::min(h->cap, std::min(2 * k1, 2 * h->ub[s + 3]));
+    }
+  }
+  CK(cudaGetLastError());
+  h->last_ntask = ng;
+  h->last_k = k;
+  return MPS_OK;
+}
+
+int prepare_tasks(mps_state* h, int ng) {
+  CK(cudaStreamSynchronize(h->stream));  // buffers may be regrown; pinned staging is reused
+  int rc = ensure_tasks(h, ng);
+  if (rc) return rc;
+  return ensure_slots(h, ng);
+}
+
+int apply_layer_impl(mps_state* h, int k, int ng, const int* sites, const double* Us) {
+  int rc = validate_layer(h, k, ng, sites, Us);
+  if (rc) return rc;
+  if (ng == 0) return MPS_OK;
+  const int d = 1 << k;
+  for (int g = 0; g < ng; ++g)
+    if (!is_unitary(Us + (size_t)2 * d * d * g, d)) return fail(MPS_ERR_NOT_UNITARY, "gate is not unitary");
+  if (k == 1) {
+    for (int g = 0; g < ng; ++g) {
+      const double* u = Us + 8 * g;
+      const int s = sites[g];
+      std::array<cd, 4> nu;
+      std::array<cd, 4> p = h->has_pend[s] ? h->pend[s] : std::array<cd, 4>{1.0, 0.0, 0.0, 1.0};
+      for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c)
+          nu[r * 2 + c] = cd(u[2 * (r * 2)], u[2 * (r * 2) + 1]) * p[c] + cd(u[2 * (r * 2 + 1)], u[2 * (r * 2 + 1) + 1]) * p[2 + c];
+      h->pend[s] = nu;
+      h->has_pend[s] = 1;
+    }
+    return MPS_OK;
+  }
+  rc = prepare_tasks(h, ng);
+  if (rc) return rc;
+  for (int g = 0; g < ng; ++g) fold_pending(h, sites[g], k, Us + (size_t)2 * d * d * g, h->h_gates + 64 * g);
+  CK(cudaMemcpyAsync(h->d_gates, h->h_gates, sizeof(double2) * 64 * ng, cudaMemcpyHostToDevice, h->stream));
+  return run_update(h, k, ng, sites, h->d_gates, 64);
+}
+
+int apply_layer_device_impl(mps_state* h, int k, int ng, const int* sites, const double* d_Us) {
+  int rc = validate_layer(h, k, ng, sites, d_Us);
+  if (rc) return rc;
+  if (ng == 0) return MPS_OK;
+  rc = flush_pending(h);
+  if (rc) return rc;
+  const int d = 1 << k;
+  if (k == 1) {
+    if (!h->d_site || !h->h_site) {
+      CK(cudaMalloc(&h->d_site, sizeof(SiteTask) * h->n));
+      CK(cudaMalloc(&h->d_site_gates, sizeof(double2) * 4 * h->n));
+      CK(cudaMallocHost(&h->h_site, sizeof(SiteTask) * h->n));
+      CK(cudaMallocHost(&h->h_site_gates, sizeof(double2) * 4 * h->n));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    int el_ub = 1;
+    for (int g = 0; g < ng; ++g) {
+      SiteTask st;
+      st.g = site_ptr(h, sites[g]);
+      st.chi = h->chi;
+      st.site = sites[g];
+      st.cap = h->cap;
+      st.U = (const double2*)d_Us + 4 * g;
+      h->h_site[g] = st;
+      el_ub = std::max(el_ub, h->ub[sites[g]] * h->ub[sites[g] + 1]);
+    }
+    CK(cudaMemcpyAsync(h->d_site, h->h_site, sizeof(SiteTask) * ng, cudaMemcpyHostToDevice, h->stream));
+    launch_apply1(h->d_site, ng, el_ub, h->stream);
+    h->launches_all += 1;
+    CK(cudaGetLastError());
+    return MPS_OK;
+  }
+  rc = prepare_tasks(h, ng);
+  if (rc) return rc;
+  return run_update(h, k, ng, sites, (const double2*)d_Us, d * d);
+}
+
+// Deferred device errors: the sticky status word (d_counter[1]) set by kernels.
+int collect_status(mps_state* h) {
+  CK(cudaStreamSynchronize(h->stream));
+  int st = 0;
+  CK(cudaMemcpy(&st, h->d_counter + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st == 0) return MPS_OK;
+  CK(cudaMemset(h->d_counter + 1, 0, sizeof(int)));
+  return fail(st, st == MPS_ERR_NOCONVERGE ? "Jacobi SVD did not converge (gate left unapplied)"
+                                           : "device error");
+}
+
+int read_chi(mps_state* h, std::vector<int>& chi) {
+  chi.resize(h->n + 1);
+  CK(cudaMemcpyAsync(chi.data(), h->chi, sizeof(int) * (h->n + 1), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return MPS_OK;
+}
+
+// Reduced density operator of `qubits` by transfer-matrix contraction.
+int rdo_impl(mps_state* h, const int* qubits, int nq, std::vector<cd>& rho) {
+  std::vector<int> pos(h->n, -1);
+  for (int t = 0; t < nq; ++t) pos[qubits[t]] = t;
+  int rc = flush_pending(h);
+  if (rc) return rc;
+  std::vector<int> chi;
+  rc = read_chi(h, chi);
+  if (rc) return rc;
+  // buffer sizes: blocks * dim^2 for E, blocks * xl * xr for tmp (x2 for open sites)
+  size_t e_max = 1, t_max = 1, s_max = 1;
+  {
+    size_t nblk = 1;
+    for (int s = 0; s < h->n; ++s) {
+      const size_t xl = chi[s], xr = chi[s + 1];
+      const size_t tb = (pos[s] >= 0 ? 2 : 1) * nblk * xl * xr;
+      if (pos[s] >= 0) nblk *= 4;
+      e_max = std::max(e_max, std::max(nblk * xr * xr, nblk * xl * xl));
+      t_max = std::max(t_max, tb);
+      s_max = std::max(s_max, 2 * xl * xr);
+    }
+  }
+  if (e_max > (size_t)1 << 27 || t_max > (size_t)1 << 27) return fail(MPS_ERR_TOO_LARGE, "reduced density too large");
+  double2 *E0 = nullptr, *E1 = nullptr, *Tm = nullptr, *Sc = nullptr;
+  auto cleanup = [&]() { cudaFree(E0); cudaFree(E1); cudaFree(Tm); cudaFree(Sc); };
+  if (cudaMalloc(&E0, e_max * sizeof(double2)) != cudaSuccess || cudaMalloc(&E1, e_max * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc(&Tm, t_max * sizeof(double2)) != cudaSuccess || cudaMalloc(&Sc, s_max * sizeof(double2)) != cudaSuccess) {
+    cleanup();
+    return fail(MPS_ERR_NOMEM, "reduced density buffers");
+  }
+  const double2 one = make_double2(1.0, 0.0);
+  cudaMemcpyAsync(E0, &one, sizeof(double2), cudaMemcpyHostToDevice, h->stream);
+  int nblk = 1;
+  for (int s = 0; s < h->n; ++s) {
+    const int xl = chi[s], xr = chi[s + 1];
+    launch_scale_site(site_ptr(h, s), bond_ptr(h, s), xl, xr, h->cap, Sc, h->stream);
+    const long long sE = (long long)xl * xl, sT = (long long)xr * xl, sN = (long long)xr * xr;
+    if (pos[s] < 0) {
+      for (int i = 0; i < 2; ++i) {
+        const double2* Ai = Sc + (size_t)i * xl * xr;
+        // tmp_b = A_i^T E_b  (xr x xl)
+        launch_zgemm(xr, xl, xl, Ai, xr, 0, 1, E0, xl, sE, 0, Tm, xl, sT, 0, nblk, h->stream);
+        // E'_b (+)= tmp_b conj(A_i)  (xr x xr)
+        launch_zgemm(xr, xr, xl, Tm, xl, sT, 0, Ai, xr, 0, 1, E1, xr, sN, i, nblk, h->stream);
+      }
+    } else {
+      for (int i = 0; i < 2; ++i)
+        launch_zgemm(xr, xl, xl, Sc + (size_t)i * xl * xr, xr, 0, 1, E0, xl, sE, 0, Tm + (size_t)i * nblk * sT, xl,
+                     sT, 0, nblk, h->stream);
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+          launch_zgemm(xr, xr, xl, Tm + (size_t)i * nblk * sT, xl, sT, 0, Sc + (size_t)j * xl * xr, xr, 0, 1,
+                       E1 + (size_t)(i * 2 + j) * nblk * sN, xr, sN, 0, nblk, h->stream);
+      nblk *= 4;
+    }
+    std::swap(E0, E1);
+  }
+  std::vector<double2> vals(nblk);
+  cudaError_t ce = cudaMemcpyAsync(vals.data(), E0, sizeof(double2) * nblk, cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (ce == cudaSuccess) ce = cudaGetLastError();
+  cleanup();
+  if (ce != cudaSuccess) return fail(MPS_ERR_CUDA, std::string("reduced density: ") + cudaGetErrorString(ce));
+  // open sites in site order; block index = sum_t (i_t*2 + j_t) 4^(t-1), t = 1..m
+  std::vector<int> open;
+  for (int s = 0; s < h->n; ++s)
+    if (pos[s] >= 0) open.push_back(s);
+  const int dim = 1 << nq;
+  rho.assign((size_t)dim * dim, cd(0));
+  cd tr = 0;
+  for (int blk = 0; blk < nblk; ++blk) {
+    int x = 0, y = 0;
+    bool diag = true;
+    for (int t = 0; t < nq; ++t) {
+      const int pr = (blk >> (2 * t)) & 3, i = pr >> 1, j = pr & 1;
+      const int sh = nq - 1 - pos[open[t]];
+      x |= i << sh;
+      y |= j << sh;
+      diag = diag && (i == j);
+    }
+    rho[(size_t)x * dim + y] = cd(vals[blk].x, vals[blk].y);
+    if (diag) tr += cd(vals[blk].x, vals[blk].y);
+  }
+  for (cd& v : rho) v /= tr.real();
+  return MPS_OK;
+}
+
+}  // namespace
+
+// ================================================================= C ABI ===
+
+extern "C" {
+
+const char* mps_last_error(void) { return g_err.c_str(); }
+
+int mps_create(int n, int chi_max, double cutoff, mps_handle* out) {
+  if (!out) return fail(MPS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > 4096) return fail(MPS_ERR_ARG, "n out of range");
+  if (chi_max < 1 || chi_max > kMaxCap) return fail(MPS_ERR_ARG, "chi_max out of range");
+  if (!(cutoff >= 0.0) || !std::isfinite(cutoff)) return fail(MPS_ERR_ARG, "cutoff must be finite and >= 0");
+  mps_state* h = new mps_state();
+  h->n = n;
+  h->cap = chi_max;
+  h->cutoff = cutoff;
+  h->pend.assign(n, std::array<cd, 4>{1.0, 0.0, 0.0, 1.0});
+  h->has_pend.assign(n, 0);
+  auto bad = [&](cudaError_t e) {
+    const int code = e == cudaErrorMemoryAllocation ? MPS_ERR_NOMEM : MPS_ERR_CUDA;
+    g_err = std::string("mps_create: ") + cudaGetErrorString(e);
+    free_state(h);
+    return code;
+  };
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
+  h->stream = h->own;
+  if ((e = cudaMalloc(&h->gamma, sizeof(double2) * gamma_elems(h))) != cudaSuccess) return bad(e);
+  if ((e = cudaMalloc(&h->lambda, sizeof(double) * (size_t)(n + 1) * chi_max)) != cudaSuccess) return bad(e);
+  if ((e = cudaMalloc(&h->chi, sizeof(int) * (n + 1))) != cudaSuccess) return bad(e);
+  if ((e = cudaMalloc(&h->d_counter, 2 * sizeof(int))) != cudaSuccess) return bad(e);
+  if ((e = cudaMemset(h->d_counter, 0, 2 * sizeof(int))) != cudaSuccess) return bad(e);
+  if ((e = cudaMallocHost(&h->h_counter, sizeof(int))) != cudaSuccess) return bad(e);
+  int rc = reset_state(h);
+  if (rc) { free_state(h); return rc; }
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bad(e);
+  *out = h;
+  return MPS_OK;
+}
+
+int mps_destroy(mps_handle h) {
+  free_state(h);
+  return MPS_OK;
+}
+
+int mps_set_stream(mps_handle h, void* s) {
+  if (!h) return fail(MPS_ERR_ARG, "NULL handle");
+  CK(cudaStreamSynchronize(h->stream));
+  h->stream = s ? (cudaStream_t)s : h->own;
+  return MPS_OK;
+}
+
+int mps_set_mode(mps_handle h, int prec, int slices, int svd_mode) {
+  if (!h) return fail(MPS_ERR_ARG, "NULL handle");
+  if (prec != MPS_PREC_FP64 && prec != MPS_PREC_SPLIT) return fail(MPS_ERR_ARG, "unknown precision mode");
+  if (slices != 0 && (slices < 3 || slices > 8)) return fail(MPS_ERR_ARG, "slices must be 0 or 3..8");
+  if (svd_mode != 0) return fail(MPS_ERR_ARG, "svd_mode must be 0");
+  if (prec == MPS_PREC_SPLIT) return fail(MPS_ERR_ARG, "split precision is not built in this library");
+  h->prec = prec;
+  h->slices = slices ? slices : 8;
+  h->svd_mode = svd_mode;
+  return MPS_OK;
+}
+
+int mps_reset(mps_handle h) {
+  if (!h) return fail(MPS_ERR_ARG, "NULL handle");
+  return reset_state(h);
+}
+
+int mps_apply_gate(mps_handle h, int site, int k, const double* U) {
+  if (!h) return fail(MPS_ERR_ARG, "NULL handle");
+  return apply_layer_impl(h, k, 1, &site, U);
+}
+
+int mps_apply_layer(mps_handle h, int k, int n_gates, const int* sites, const double* Us) {
+  if (!h) return fail(MPS_ERR_ARG, "NULL handle");
+  return apply_layer_impl(h, k, n_gates, sites, Us);
+}
+
+int mps_apply_layer_device(mps_handle h, int k, int n_gates, const int* sites, const double* d_Us) {
+  if (!h) return fail(MPS_ERR_ARG, "NULL handle");
+  return apply_layer_device_impl(h, k, n_gates, sites, d_Us);
+}
+
+int mps_profile(mps_handle h, int enable) {
+  if (!h) return fail(MPS_ERR_ARG, "NULL handle");
+  CK(cudaStreamSynchronize(h->stream));
+  if (!h->d_prof_flops) CK(cudaMalloc(&h->d_prof_flops, 4 * sizeof(unsigned long long)));
+  CK(cudaMemset(h->d_prof_flops, 0, 4 * sizeof(unsigned long long)));
+  h->prof = enable ? 1 : 0;
+  h->ev_next = 0;
+  h->prof_rec.clear();
+  for (int i = 0; i < 4; ++i) {
+    h->prof_flops_host[i] = 0.0;
+    h->prof_launch[i] = 0;
+  }
+  h->launches_all = 0;
+  return MPS_OK;
+}
+
+int mps_profile_read(mps_handle h, int kernel, double* ms, long long* launches, double* flops,
+                     long long* launches_all) {
+  if (!h || kernel < 0 || kernel > 3) return fail(MPS_ERR_ARG, "bad arguments");
+  CK(cudaStreamSynchronize(h->stream));
+  double tot = 0.0;
+  for (const auto& r : h->prof_rec) {
+    if (r[0] != kernel) continue;
+    float m = 0.f;
+    CK(cudaEventElapsedTime(&m, h->evs[r[1]], h->evs[r[2]]));
+    tot += m;
+  }
+  unsigned long long dev[4] = {0, 0, 0, 0};
+  if (h->d_prof_flops) CK(cudaMemcpy(dev, h->d_prof_flops, sizeof(dev), cudaMemcpyDeviceToHost));
+  if (ms) *ms = tot;
+  if (launches) *launches = h->prof_launch[kernel];
+  if (flops) *flops = (double)dev[kernel] + h->prof_flops_host[kernel];
+  if (launches_all) *launches_all = h->launches_all;
+  return MPS_OK;
+}
+
+int mps_amplitudes(mps_handle h, int count, const unsigned char* bits, double* out) {
+  if (!h || !bits || !out || count < 0) return fail(MPS_ERR_ARG, "bad arguments");
+  if (count == 0) return MPS_OK;
+  int rc = flush_pending(h);
+  if (rc) return rc;
+  unsigned char* d_bits = nullptr;
+  double2* d_out = nullptr;
+  CK(cudaMalloc(&d_bits, (size_t)count * h->n));
+  if (cudaMalloc(&d_out, sizeof(double2) * count) != cudaSuccess) {
+    cudaFree(d_bits);
+    return fail(MPS_ERR_NOMEM, "amplitude buffers");
+  }
+  cudaError_t e = cudaMemcpyAsync(d_bits, bits, (size_t)count * h->n, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) {
+    launch_amplitudes(h->gamma, h->lambda, h->chi, h->n, h->cap, d_bits, count, d_out, h->stream);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, sizeof(double2) * count, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d_bits);
+  cudaFree(d_out);
+  if (e != cudaSuccess) return fail(MPS_ERR_CUDA, std::string("amplitudes: ") + cudaGetErrorString(e));
+  return collect_status(h);
+}
+
+int mps_amplitude(mps_handle h, const unsigned char* bits, double* out) { return mps_amplitudes(h, 1, bits, out); }
+
+int mps_reduced_density(mps_handle h, const int* qubits, int nq, double* rho) {
+  if (!h || !qubits || !rho) return fail(MPS_ERR_ARG, "bad arguments");
+  if (nq < 1) return fail(MPS_ERR_ARG, "nq must be >= 1");
+  if (nq > 6) return fail(MPS_ERR_TOO_LARGE, "nq > 6");
+  std::vector<char> seen(h->n, 0);
+  for (int t = 0; t < nq; ++t) {
+    if (qubits[t] < 0 || qubits[t] >= h->n || seen[qubits[t]]) return fail(MPS_ERR_ARG, "bad qubit list");
+    seen[qubits[t]] = 1;
+  }
+  std::vector<cd> r;
+  int rc = rdo_impl(h, qubits, nq, r);
+  if (rc) return rc;
+  for (size_t e = 0; e < r.size(); ++e) {
+    rho[2 * e] = r[e].real();
+    rho[2 * e + 1] = r[e].imag();
+  }
+  return collect_status(h);
+}
+
+int mps_expectation(mps_handle h, int site, int k, const double* O, double* out) {
+  if (!h || !O || !out) return fail(MPS_ERR_ARG, "bad arguments");
+  if (k < 1 || k > 3 || site < 0 || site + k > h->n) return fail(MPS_ERR_ARG, "operator range");
+  int q[3];
+  for (int j = 0; j < k; ++j) q[j] = site + j;
+  std::vector<cd> r;
+  int rc = rdo_impl(h, q, k, r);
+  if (rc) return rc;
+  const int d = 1 << k;
+  cd acc = 0;
+  for (int x = 0; x < d; ++x)
+    for (int y = 0; y < d; ++y) acc += r[(size_t)x * d + y] * cd(O[2 * (y * d + x)], O[2 * (y * d + x) + 1]);
+  out[0] = acc.real();
+  out[1] = acc.imag();
+  return collect_status(h);
+}
+
+int mps_get_schmidt(mps_handle h, int bond, double* lambda, int* len) {
+  if (!h || !lambda || !len) return fail(MPS_ERR_ARG, "bad arguments");
+  if (bond < 0 || bond > h->n - 2) return fail(MPS_ERR_ARG, "bond out of range");
+  int c = 0;
+  CK(cudaMemcpyAsync(&c, h->chi + bond + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(lambda, bond_ptr(h, bond), sizeof(double) * c, cudaMemcpyDeviceToHost));
+  *len = c;
+  return collect_status(h);
+}
+
+int mps_bond_dims(mps_handle h, int* chi) {
+  if (!h || !chi) return fail(MPS_ERR_ARG, "bad arguments");
+  std::vector<int> c;
+  int rc = read_chi(h, c);
+  if (rc) return rc;
+  for (int b = 0; b < h->n - 1; ++b) chi[b] = c[b + 1];
+  return collect_status(h);
+}
+
+int mps_export(mps_handle h, int* chi, double* gammas, double* lambdas) {
+  if (!h || !chi) return fail(MPS_ERR_ARG, "bad arguments");
+  int rc = flush_pending(h);
+  if (rc) return rc;
+  std::vector<int> c;
+  rc = read_chi(h, c);
+  if (rc) return rc;
+  for (int b = 0; b <= h->n; ++b) chi[b] = c[b];
+  if (gammas) {
+    size_t off = 0;
+    for (int s = 0; s < h->n; ++s)
+      for (int i = 0; i < 2; ++i) {
+        const size_t xl = c[s], xr = c[s + 1];
+        CK(cudaMemcpy2DAsync(gammas + 2 * off, xr * sizeof(double2), site_ptr(h, s) + (size_t)i * h->cap * h->cap,
+                             h->cap * sizeof(double2), xr * sizeof(double2), xl, cudaMemcpyDeviceToHost, h->stream));
+        off += xl * xr;
+      }
+  }
+  if (lambdas) {
+    size_t off = 0;
+    for (int b = 0; b < h->n - 1; ++b) {
+      CK(cudaMemcpyAsync(lambdas + off, bond_ptr(h, b), sizeof(double) * c[b + 1], cudaMemcpyDeviceToHost, h->stream));
+      off += c[b + 1];
+    }
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return collect_status(h);
+}
+
+int mps_import(mps_handle h, const int* chi, const double* gammas, const double* lambdas) {
+  if (!h || !chi || !gammas || (h->n > 1 && !lambdas)) return fail(MPS_ERR_ARG, "bad arguments");
+  if (chi[0] != 1 || chi[h->n] != 1) return fail(MPS_ERR_ARG, "boundary bonds must be 1");
+  for (int b = 0; b <= h->n; ++b)
+    if (chi[b] < 1 || chi[b] > h->cap) return fail(MPS_ERR_ARG, "bond dimension out of [1, chi_max]");
+  CK(cudaStreamSynchronize(h->stream));
+  int rc = reset_state(h);
+  if (rc) return rc;
+  size_t off = 0;
+  for (int s = 0; s < h->n; ++s)
+    for (int i = 0; i < 2; ++i) {
+      const size_t xl = chi[s], xr = chi[s + 1];
+      CK(cudaMemcpy2DAsync(site_ptr(h, s) + (size_t)i * h->cap * h->cap, h->cap * sizeof(double2), gammas + 2 * off,
+                           xr * sizeof(double2), xr * sizeof(double2), xl, cudaMemcpyHostToDevice, h->stream));
+      off += xl * xr;
+    }
+  size_t lo = 0;
+  for (int b = 0; b < h->n - 1; ++b) {
+    CK(cudaMemcpyAsync(bond_ptr(h, b), lambdas + lo, sizeof(double) * chi[b + 1], cudaMemcpyHostToDevice, h->stream));
+    lo += chi[b + 1];
+  }
+  CK(cudaMemcpyAsync(h->chi, chi, sizeof(int) * (h->n + 1), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->ub.assign(chi, chi + h->n + 1);
+  return MPS_OK;
+}
+
+int mps_diag(mps_handle h, int cap, int* count, int* k, double* discarded, int* sweeps) {
+  if (!h || !count || cap < 0) return fail(MPS_ERR_ARG, "bad arguments");
+  CK(cudaStreamSynchronize(h->stream));
+  *count = h->last_ntask;
+  const int m = std::min(cap, h->last_ntask);
+  if (m > 0) {
+    std::vector<TaskMeta> t(m);
+    CK(cudaMemcpy(t.data(), h->d_meta, sizeof(TaskMeta) * m, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < m; ++i) {
+      if (k) k[i] = t[i].knew;
+      if (discarded) discarded[i] = t[i].disc;
+      if (sweeps) sweeps[i] = t[i].sweeps_total;
+    }
+  }
+  return MPS_OK;
+}
+
+int mps_sync(mps_handle h) {
+  if (!h) return fail(MPS_ERR_ARG, "NULL handle");
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  return collect_status(h);
+}
+
+}  // extern "C"

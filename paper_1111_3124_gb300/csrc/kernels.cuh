@@ -1,0 +1,34 @@
+// Host-side launch wrappers of the engine's kernels (all asynchronous on `st`).
+#pragma once
+#include "engine.cuh"
+
+namespace mpsgb {
+
+constexpr int kBlockW = 8;  // Jacobi block width b (columns per block)
+
+void launch_setup(const GateTask* t, TaskMeta* m, int ntask, int stage, cudaStream_t st);
+void launch_contract2(const GateTask* t, const TaskMeta* m, int ntask, int a_ub, int b_ub, cudaStream_t st);
+void launch_contract3(const GateTask* t, const TaskMeta* m, int ntask, int x0_ub, int xl_ub, int xr_ub,
+                      cudaStream_t st);
+void launch_frob(const GateTask* t, TaskMeta* m, int ntask, long long el_ub, int second, cudaStream_t st);
+void launch_init_V(const GateTask* t, const TaskMeta* m, int ntask, int nw_ub, cudaStream_t st);
+void launch_jacobi_round(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub, int second,
+                         unsigned long long* flops, cudaStream_t st);
+void launch_sweep_end(TaskMeta* m, int ntask, int max_sweeps, int* active_count, cudaStream_t st);
+void launch_colnorms(const GateTask* t, const TaskMeta* m, int ntask, int nw_ub, int second, cudaStream_t st);
+void launch_truncate(const GateTask* t, TaskMeta* m, int ntask, int stage, int chi_cap, cudaStream_t st);
+void launch_emit_left(const GateTask* t, const TaskMeta* m, int ntask, int r_ub, int k_ub, int stage,
+                      cudaStream_t st);
+void launch_emit_right(const GateTask* t, const TaskMeta* m, int ntask, int cn_ub, int k_ub, int stage,
+                       cudaStream_t st);
+void launch_form_second(const GateTask* t, const TaskMeta* m, int ntask, int k1_ub, int xr_ub, cudaStream_t st);
+void launch_apply1(const SiteTask* t, int ntask, int el_ub, cudaStream_t st);
+
+void launch_amplitudes(const double2* gamma, const double* lambda, const int* chi, int n, int cap,
+                       const unsigned char* bits, int count, double2* out, cudaStream_t st);
+void launch_scale_site(const double2* g, const double* lam, int xl, int xr, int cap, double2* out, cudaStream_t st);
+void launch_zgemm(int M, int N, int K, const double2* A, int lda, long long sA, int transA, const double2* B,
+                  int ldb, long long sB, int conjB, double2* C, int ldc, long long sC, int accumulate, int batch,
+                  cudaStream_t st);
+
+}  // namespace mpsgb

@@ -1,0 +1,276 @@
+"""Thin ctypes binding of the C ABI declared in include/mps.h.
+
+Every step of the gate update runs in the CUDA library libmps_gb300.so; this
+module only converts arguments. There is no CPU fallback: importing it
+without the built library, or using it without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmps_gb300.so")
+
+MPS_OK = 0
+MPS_ERR_ARG = -1
+MPS_ERR_NOMEM = -2
+MPS_ERR_CUDA = -3
+MPS_ERR_NOCONVERGE = -4
+MPS_ERR_TIMEOUT = -5
+MPS_ERR_NOT_UNITARY = -6
+MPS_ERR_TOO_LARGE = -7
+PREC_FP64 = 0
+PREC_SPLIT = 1
+
+# every symbol include/mps.h declares
+EXPORTS = [
+    "mps_create", "mps_destroy", "mps_set_stream", "mps_set_mode", "mps_reset", "mps_apply_gate",
+    "mps_apply_layer", "mps_apply_layer_device", "mps_profile", "mps_profile_read", "mps_amplitude", "mps_amplitudes", "mps_expectation", "mps_reduced_density",
+    "mps_get_schmidt", "mps_bond_dims", "mps_export", "mps_import", "mps_diag", "mps_sync", "mps_last_error",
+]
+
+
+class MPSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (status %d)" % (msg, code))
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libmps_gb300.so is not built: run __graft_entry__.build() "
+                          "(there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    dp, ip = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    bp = ctypes.c_char_p
+    sig = {
+        "mps_create": [I, I, D, ctypes.POINTER(P)],
+        "mps_destroy": [P],
+        "mps_set_stream": [P, P],
+        "mps_set_mode": [P, I, I, I],
+        "mps_reset": [P],
+        "mps_apply_gate": [P, I, I, dp],
+        "mps_apply_layer": [P, I, I, ip, dp],
+        "mps_apply_layer_device": [P, I, I, ip, P],
+        "mps_profile": [P, I],
+        "mps_profile_read": [P, I, dp, ctypes.POINTER(ctypes.c_longlong), dp, ctypes.POINTER(ctypes.c_longlong)],
+        "mps_amplitude": [P, bp, dp],
+        "mps_amplitudes": [P, I, bp, dp],
+        "mps_expectation": [P, I, I, dp, dp],
+        "mps_reduced_density": [P, ip, I, dp],
+        "mps_get_schmidt": [P, I, dp, ip],
+        "mps_bond_dims": [P, ip],
+        "mps_export": [P, ip, dp, dp],
+        "mps_import": [P, ip, dp, dp],
+        "mps_diag": [P, I, ip, ip, dp, ip],
+        "mps_sync": [P],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = I
+    L.mps_last_error.restype = ctypes.c_char_p
+    L.mps_last_error.argtypes = []
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _c128(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+def check(rc: int):
+    if rc != MPS_OK:
+        raise MPSError(rc, load_library().mps_last_error().decode(errors="replace"))
+
+
+class MPS:
+    """An n-qubit MPS in Vidal form on the current CUDA device (|0...0> at creation)."""
+
+    def __init__(self, n: int, chi_max: int, cutoff: float, prec: int = PREC_FP64, stream=None):
+        L = load_library()
+        h = ctypes.c_void_p()
+        check(L.mps_create(n, chi_max, float(cutoff), ctypes.byref(h)))
+        self._h = h
+        self.n, self.chi_max, self.cutoff = n, chi_max, cutoff
+        if prec != PREC_FP64:
+            self.set_mode(prec)
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load_library().mps_destroy(h)
+        self._h = None
+
+    __del__ = close
+
+    def set_stream(self, stream) -> None:
+        """stream: a torch.cuda.Stream, an integer cudaStream_t, or None."""
+        ptr = getattr(stream, "cuda_stream", stream)
+        check(load_library().mps_set_stream(self._h, ctypes.c_void_p(ptr) if ptr else None))
+
+    def set_mode(self, prec: int, slices: int = 0, svd_mode: int = 0) -> None:
+        check(load_library().mps_set_mode(self._h, prec, slices, svd_mode))
+
+    def reset(self) -> None:
+        check(load_library().mps_reset(self._h))
+
+    def apply_gate(self, site: int, U) -> None:
+        U = _c128(U)
+        k = {2: 1, 4: 2, 8: 3}[U.shape[0]]
+        check(load_library().mps_apply_gate(self._h, site, k, _dp(U.view(np.float64))))
+
+    def apply_layer(self, sites, Us) -> None:
+        Us = _c128(Us)
+        k = {2: 1, 4: 2, 8: 3}[Us.shape[-1]]
+        s = np.ascontiguousarray(np.asarray(sites, dtype=np.int32))
+        check(load_library().mps_apply_layer(self._h, k, len(s), _ip(s), _dp(Us.view(np.float64))))
+
+    def apply_layer_device(self, sites, d_Us, k: int) -> None:
+        """Gates already in device memory: d_Us is a CUDA tensor (complex128,
+        shape (n_gates, 2^k, 2^k), contiguous) or an integer device address."""
+        ptr = d_Us.data_ptr() if hasattr(d_Us, "data_ptr") else int(d_Us)
+        s = np.ascontiguousarray(np.asarray(sites, dtype=np.int32))
+        check(load_library().mps_apply_layer_device(self._h, k, len(s), _ip(s), ctypes.c_void_p(ptr)))
+
+    def profile(self, enable: bool) -> None:
+        check(load_library().mps_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self, kernel: int):
+        ms, fl = ctypes.c_double(), ctypes.c_double()
+        nl, na = ctypes.c_longlong(), ctypes.c_longlong()
+        check(load_library().mps_profile_read(self._h, kernel, ctypes.byref(ms), ctypes.byref(nl),
+                                              ctypes.byref(fl), ctypes.byref(na)))
+        return {"ms": ms.value, "launches": nl.value, "flops": fl.value, "launches_all": na.value}
+
+    def apply_gate_on(self, qubits, U) -> None:
+        """Gate on listed qubits (first = most significant index bit): adjacent
+        increasing qubits directly; a two-qubit gate on (q, q+-2) as a U(8) on
+        (q, q+1, q+2) with the identity on the middle qubit."""
+        U = _c128(U)
+        q = list(qubits)
+        if len(q) == 1 or all(q[t + 1] == q[t] + 1 for t in range(len(q) - 1)):
+            self.apply_gate(q[0], U)
+            return
+        if len(q) == 2 and abs(q[1] - q[0]) == 2:
+            T = U.reshape(2, 2, 2, 2)
+            if q[0] > q[1]:
+                T = T.transpose(1, 0, 3, 2)
+            U8 = np.einsum("ijkl,mn->imjknl", T, np.eye(2)).reshape(8, 8)
+            self.apply_gate(min(q), U8)
+            return
+        raise NotImplementedError("only adjacent gates and distance-2 two-qubit gates")
+
+    def amplitudes(self, bits) -> np.ndarray:
+        b = np.ascontiguousarray(np.asarray(bits, dtype=np.uint8).reshape(-1, self.n))
+        out = np.zeros((b.shape[0], 2))
+        check(load_library().mps_amplitudes(self._h, b.shape[0], b.ctypes.data_as(ctypes.c_char_p), _dp(out)))
+        return out[:, 0] + 1j * out[:, 1]
+
+    def amplitude(self, bits) -> complex:
+        return complex(self.amplitudes(np.asarray(bits).reshape(1, -1))[0])
+
+    def expectation(self, site: int, O) -> complex:
+        O = _c128(O)
+        k = {2: 1, 4: 2, 8: 3}[O.shape[0]]
+        out = np.zeros(2)
+        check(load_library().mps_expectation(self._h, site, k, _dp(O.view(np.float64)), _dp(out)))
+        return complex(out[0], out[1])
+
+    def reduced_density(self, qubits) -> np.ndarray:
+        q = np.ascontiguousarray(np.asarray(qubits, dtype=np.int32))
+        d = 1 << len(q)
+        rho = np.zeros((d, d), dtype=np.complex128)
+        check(load_library().mps_reduced_density(self._h, _ip(q), len(q), _dp(rho.view(np.float64))))
+        return rho
+
+    def reduced_density_block(self, first: int, last: int) -> np.ndarray:
+        return self.reduced_density(list(range(first, last + 1)))
+
+    def schmidt(self, bond: int) -> np.ndarray:
+        out = np.zeros(self.chi_max)
+        ln = ctypes.c_int()
+        check(load_library().mps_get_schmidt(self._h, bond, _dp(out), ctypes.byref(ln)))
+        return out[:ln.value].copy()
+
+    def bond_dims(self) -> np.ndarray:
+        c = np.zeros(max(self.n - 1, 1), dtype=np.int32)
+        check(load_library().mps_bond_dims(self._h, _ip(c)))
+        return c[:self.n - 1]
+
+    def export(self):
+        chi = np.zeros(self.n + 1, dtype=np.int32)
+        L = load_library()
+        check(L.mps_export(self._h, _ip(chi), None, None))
+        ng = sum(2 * int(chi[s]) * int(chi[s + 1]) for s in range(self.n))
+        nl = sum(int(chi[b + 1]) for b in range(self.n - 1))
+        g = np.zeros(ng, dtype=np.complex128)
+        lam = np.zeros(max(nl, 1))
+        check(L.mps_export(self._h, _ip(chi), _dp(g.view(np.float64)), _dp(lam)))
+        gammas, off = [], 0
+        for s in range(self.n):
+            sz = 2 * int(chi[s]) * int(chi[s + 1])
+            gammas.append(g[off:off + sz].reshape(2, int(chi[s]), int(chi[s + 1])).copy())
+            off += sz
+        lams, off = [], 0
+        for b in range(self.n - 1):
+            lams.append(lam[off:off + int(chi[b + 1])].copy())
+            off += int(chi[b + 1])
+        return chi, gammas, lams
+
+    def import_state(self, gammas, lams) -> None:
+        chi = np.ascontiguousarray(np.array([1] + [g.shape[2] for g in gammas], dtype=np.int32))
+        g = _c128(np.concatenate([np.ravel(x) for x in gammas]))
+        lam = np.ascontiguousarray(np.concatenate([np.ravel(x) for x in lams]) if lams else np.zeros(1))
+        check(load_library().mps_import(self._h, _ip(chi), _dp(g.view(np.float64)), _dp(lam)))
+
+    def diag(self):
+        cnt = ctypes.c_int()
+        L = load_library()
+        check(L.mps_diag(self._h, 0, ctypes.byref(cnt), None, None, None))
+        m = cnt.value
+        k = np.zeros(max(m, 1), dtype=np.int32)
+        w = np.zeros(max(m, 1))
+        sw = np.zeros(max(m, 1), dtype=np.int32)
+        check(L.mps_diag(self._h, m, ctypes.byref(cnt), _ip(k), _dp(w), _ip(sw)))
+        return {"k": k[:m], "discarded": w[:m], "sweeps": sw[:m]}
+
+    def sync(self) -> None:
+        check(load_library().mps_sync(self._h))
+
+    def run_layers(self, layers) -> int:
+        """Applies a circuit given as layers of (site, U); same-size gates of a
+        layer go through one batched mps_apply_layer call. Returns the number of
+        multi-qubit updates."""
+        nup = 0
+        for layer in layers:
+            by_k = {}
+            for site, U in layer:
+                by_k.setdefault(U.shape[0], []).append((site, U))
+            for d in sorted(by_k):
+                gs = by_k[d]
+                self.apply_layer([s for s, _ in gs], np.stack([_c128(U) for _, U in gs]))
+                if d >= 4:
+                    nup += len(gs)
+        return nup

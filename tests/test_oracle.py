@@ -296,3 +296,16 @@ def test_single_truncation_fidelity_equals_kept_weight():
     v = mps_vector(trunc, n)
     f = abs(np.vdot(sv.vector(), v)) ** 2
     assert abs(f - (1 - w)) < 1e-12
+
+
+def test_numerically_zero_values_dropped_with_zero_cutoff():
+    """Exact zeros of a rank-deficient theta (a product gate on a product
+    state) are dropped even with cutoff 0: the bond stays rank one and the
+    state is exact."""
+    m = oracle.OracleMPS(4, 16, 0.0)
+    U = np.kron(C.H, C.H)
+    m.apply_gate(1, U)
+    assert [m.bond_dim(b) for b in range(3)] == [1, 1, 1]
+    sv = StateVector(4)
+    sv.apply([1, 2], U)
+    np.testing.assert_allclose(mps_vector(m, 4), sv.vector(), atol=1e-15)
