@@ -200,6 +200,38 @@ int mps_profile_read(mps_handle h, int kernel, double* ms, long long* launches, 
  * error (MPS_ERR_NOCONVERGE, MPS_ERR_TIMEOUT, MPS_ERR_CUDA), clearing it. */
 int mps_sync(mps_handle h);
 
+/* mps_gate2_update_noalloc - one two-site (U(4)) gate update, the same
+ * computation as mps_apply_gate with k = 2, applied to tensors the caller
+ * keeps in device memory, WITHOUT ALLOCATING ANYTHING. The paper has no
+ * counterpart; it serves callers that cannot allocate device memory while
+ * they run: programs whose allocator already holds the device's memory
+ * budget, or loops that must not stall on cudaMalloc/cudaFree (both may
+ * synchronise the whole device). Its working storage is a fixed file-scope
+ * device array of about 520 KB, present on every device that loads this
+ * library until the process exits; no cudaMalloc, cudaFree or allocating
+ * library routine is called.
+ *   d_gamma_l   Gamma_s,     [2][chi_max][chi_max] complex128, device, rewritten
+ *   d_gamma_r   Gamma_{s+1}, same layout, device, rewritten
+ *   d_lambda_l  Lambda_{s-1}, chi_max doubles, device ([1] at the left end)
+ *   d_lambda_m  Lambda_s, chi_max doubles, device, rewritten
+ *   d_lambda_r  Lambda_{s+1}, chi_max doubles, device ([1] at the right end)
+ *   d_chi       3 ints on the device: chi_{s-1}, chi_s, chi_{s+1}, each in
+ *               [1, chi_max]; chi_s is rewritten with the kept rank
+ *   chi_max     capacity and truncation limit, 1 <= chi_max <= 64
+ *   cutoff      truncation threshold as in mps_create
+ *   U           host pointer, 4 x 4 complex128 row-major (not checked for unitarity)
+ *   stream      cudaStream_t to run on (NULL = the legacy default stream)
+ * The first call on a device looks up that device's scratch address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and each call clears what must start at
+ * zero; calls that overlap on the GPU (other streams, other threads) race on
+ * it and must be serialised by the caller. Synchronises `stream`.
+ * Errors: MPS_ERR_ARG, MPS_ERR_TOO_LARGE (chi_max > 64), MPS_ERR_CUDA,
+ * MPS_ERR_NOCONVERGE (tensors left unchanged). */
+int mps_gate2_update_noalloc(double* d_gamma_l, double* d_gamma_r, const double* d_lambda_l, double* d_lambda_m,
+                             const double* d_lambda_r, int* d_chi, int chi_max, double cutoff, const double* U,
+                             void* stream);
+
 /* Message describing the last error returned on the calling thread. */
 const char* mps_last_error(void);
 

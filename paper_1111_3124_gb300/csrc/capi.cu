@@ -54,6 +54,8 @@ struct Slot {
 
 }  // namespace
 
+void mpsgb::set_error_message(const char* msg) { g_err = msg; }
+
 struct mps_state {
   int n = 0, cap = 0;
   double cutoff = 0.0;

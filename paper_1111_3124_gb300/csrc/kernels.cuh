@@ -6,6 +6,9 @@ namespace mpsgb {
 
 constexpr int kBlockW = 8;  // Jacobi block width b (columns per block)
 
+// Sets the message returned by mps_last_error() on the calling thread.
+void set_error_message(const char* msg);
+
 void launch_setup(const GateTask* t, TaskMeta* m, int ntask, int stage, cudaStream_t st);
 void launch_contract2(const GateTask* t, const TaskMeta* m, int ntask, int a_ub, int b_ub, cudaStream_t st);
 void launch_contract3(const GateTask* t, const TaskMeta* m, int ntask, int x0_ub, int xl_ub, int xr_ub,

@@ -30,6 +30,7 @@ EXPORTS = [
     "mps_create", "mps_destroy", "mps_set_stream", "mps_set_mode", "mps_reset", "mps_apply_gate",
     "mps_apply_layer", "mps_apply_layer_device", "mps_profile", "mps_profile_read", "mps_amplitude", "mps_amplitudes", "mps_expectation", "mps_reduced_density",
     "mps_get_schmidt", "mps_bond_dims", "mps_export", "mps_import", "mps_diag", "mps_sync", "mps_last_error",
+    "mps_gate2_update_noalloc",
 ]
 
 
@@ -75,6 +76,7 @@ def load_library(path: str = LIB_PATH):
         "mps_import": [P, ip, dp, dp],
         "mps_diag": [P, I, ip, ip, dp, ip],
         "mps_sync": [P],
+        "mps_gate2_update_noalloc": [P, P, P, P, P, P, I, D, dp, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -274,3 +276,17 @@ class MPS:
                 if d >= 4:
                     nup += len(gs)
         return nup
+
+
+def gate2_update_noalloc(gamma_l, gamma_r, lambda_l, lambda_m, lambda_r, chi, chi_max: int, cutoff: float, U,
+                         stream=None) -> None:
+    """Two-site update on caller-owned CUDA tensors (torch tensors: complex128
+    [2, chi_max, chi_max] Gammas, float64 [chi_max] Lambdas, int32 [3] chi),
+    with no device allocation by the library (see include/mps.h)."""
+    U = _c128(U)
+    s = getattr(stream, "cuda_stream", stream)
+    check(load_library().mps_gate2_update_noalloc(
+        ctypes.c_void_p(gamma_l.data_ptr()), ctypes.c_void_p(gamma_r.data_ptr()),
+        ctypes.c_void_p(lambda_l.data_ptr()), ctypes.c_void_p(lambda_m.data_ptr()),
+        ctypes.c_void_p(lambda_r.data_ptr()), ctypes.c_void_p(chi.data_ptr()), chi_max, float(cutoff),
+        _dp(U.view(np.float64)), ctypes.c_void_p(s) if s else None))
