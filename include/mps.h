@@ -182,10 +182,12 @@ int mps_diag(mps_handle h, int cap, int* count, int* k, double* discarded, int* 
 /* Per-kernel-class timing of later calls (not part of the method; used to
  * measure each kernel against its roofline). enable = 1 brackets every launch
  * of the classes below with CUDA events on the handle's stream and counts the
- * executed binary64 flops; enable = 0 stops; each call clears the counters.
- * Kernel classes: 0 = Jacobi pair rotations, 1 = theta contraction,
- * 2 = truncation and tensor rewrite (norms, truncate, emit), 3 = split-
- * precision products. */
+ * executed flops; enable = 0 stops; each call clears the counters.
+ * Kernel classes: 0 = binary64 Jacobi pair rotations, 1 = binary64 theta
+ * contraction, 2 = truncation and tensor rewrite (norms, truncate, emit),
+ * 3 = split-precision products (tensor-core flops), 4 = fp32 Jacobi pair
+ * rotations (split mode), 5 = split-mode element-wise steps (gate mix,
+ * conversions, Newton-Schulz update). */
 int mps_profile(mps_handle h, int enable);
 
 /* Reads the counters of class `kernel`: summed launch durations in ms, the
@@ -231,6 +233,21 @@ int mps_sync(mps_handle h);
 int mps_gate2_update_noalloc(double* d_gamma_l, double* d_gamma_r, const double* d_lambda_l, double* d_lambda_m,
                              const double* d_lambda_r, int* d_chi, int chi_max, double cutoff, const double* U,
                              void* stream);
+
+/* mps_split_zgemm - C = A B for complex128 matrices in DEVICE memory,
+ * column-major (A[r + k lda], B[k + n ldb], C[r + n ldc]), computed by the
+ * split-precision scheme of MPS_PREC_SPLIT: each row of A and column of B is
+ * scaled by a power of two and cut into `slices` signed 7-bit bf16 digits,
+ * the slice products run on the tcgen05 tensor cores with exact fp32
+ * accumulation, and the binary64 result is reassembled (Ozaki et al. 2012).
+ * With 8 slices the result is binary64-accurate relative to |A||B|.
+ *   M, N >= 1; 1 <= K <= 512 (exactness of the fp32 sums); slices 1..8
+ *   stream  cudaStream_t (NULL = legacy default stream); synchronised.
+ * Not a paper entry point: the building block of the split-precision update,
+ * exposed for tests and reuse. Errors: MPS_ERR_ARG, MPS_ERR_TOO_LARGE,
+ * MPS_ERR_NOMEM, MPS_ERR_CUDA, MPS_ERR_TIMEOUT (a bounded device wait ran out). */
+int mps_split_zgemm(int M, int N, int K, const double* dA, long long lda, const double* dB, long long ldb,
+                    double* dC, long long ldc, int slices, void* stream);
 
 /* Message describing the last error returned on the calling thread. */
 const char* mps_last_error(void);

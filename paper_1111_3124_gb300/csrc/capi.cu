@@ -21,6 +21,7 @@
 #include "../../include/mps.h"
 #include "engine.cuh"
 #include "kernels.cuh"
+#include "ozaki.cuh"
 
 using namespace mpsgb;
 typedef std::complex<double> cd;
@@ -44,12 +45,20 @@ int fail(int code, const std::string& msg) {
 
 constexpr int kMaxSweeps = 40;
 
+constexpr int kProfKinds = 6;  // see mps_profile in include/mps.h
+constexpr int kSplitMaxCap = 256;  // split GEMM needs 2K <= 1024 (K <= 2 chi_max)
+constexpr int kF32Sweeps = 30;
+
 struct Slot {
   double2* A = nullptr;
   double2* V = nullptr;
   double2* T = nullptr;
   double* sigma = nullptr;
   int* perm = nullptr;
+  float2* A32 = nullptr;  // split-precision buffers, allocated on first use
+  float2* V32 = nullptr;
+  double2* P = nullptr;
+  double2* Q = nullptr;
 };
 
 }  // namespace
@@ -87,10 +96,15 @@ struct mps_state {
   std::vector<cudaEvent_t> evs;
   size_t ev_next = 0;
   std::vector<std::array<int, 3>> prof_rec;  // (class, begin event, end event)
-  double prof_flops_host[4] = {0, 0, 0, 0};
-  long long prof_launch[4] = {0, 0, 0, 0};
+  double prof_flops_host[kProfKinds] = {0, 0, 0, 0, 0, 0};
+  long long prof_launch[kProfKinds] = {0, 0, 0, 0, 0, 0};
   long long launches_all = 0;
   unsigned long long* d_prof_flops = nullptr;  // device counters, one per class
+  // split precision
+  OzJob* d_oz_jobs = nullptr;
+  int oz_cap = 0;
+  OzBuffers oz_buf;
+  int* d_oz_err = nullptr;
 };
 
 namespace {
@@ -171,6 +185,15 @@ int ensure_slots(mps_state* h, int nslot) {
     CK(cudaMalloc(&s.perm, sizeof(int) * 2 * h->cap));
     h->slots.push_back(s);
   }
+  if (h->prec == MPS_PREC_SPLIT)
+    for (int i = 0; i < nslot; ++i) {
+      Slot& s = h->slots[i];
+      if (s.A32) continue;
+      CK(cudaMalloc(&s.A32, sizeof(float2) * 4 * c2));
+      CK(cudaMalloc(&s.V32, sizeof(float2) * 4 * c2));
+      CK(cudaMalloc(&s.P, sizeof(double2) * 4 * c2));
+      CK(cudaMalloc(&s.Q, sizeof(double2) * 4 * c2));
+    }
   return MPS_OK;
 }
 
@@ -179,7 +202,9 @@ void free_state(mps_state* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (Slot& s : h->slots) {
     cudaFree(s.A); cudaFree(s.V); cudaFree(s.T); cudaFree(s.sigma); cudaFree(s.perm);
+    cudaFree(s.A32); cudaFree(s.V32); cudaFree(s.P); cudaFree(s.Q);
   }
+  cudaFree(h->d_oz_jobs); cudaFree(h->d_oz_err); cudaFree(h->oz_buf.base);
   cudaFree(h->gamma); cudaFree(h->lambda); cudaFree(h->chi);
   cudaFree(h->d_tasks); cudaFree(h->d_meta); cudaFree(h->d_gates); cudaFree(h->d_counter);
   cudaFree(h->d_site); cudaFree(h->d_site_gates);
@@ -263,9 +288,11 @@ int flush_pending(mps_state* h) {
 // Blocked one-sided Jacobi on every task's working matrix (A, or T for the
 // second split of a three-site update). One launch per round-robin round;
 // a sweep ends with a convergence count read back to the host.
-int run_svd(mps_state* h, int ntask, int nw_ub, int second) {
-  launch_init_V(h->d_tasks, h->d_meta, ntask, nw_ub, h->stream);
-  h->launches_all += 1;
+int run_svd(mps_state* h, int ntask, int nw_ub, int second, bool init_v = true) {
+  if (init_v) {
+    launch_init_V(h->d_tasks, h->d_meta, ntask, nw_ub, h->stream);
+    h->launches_all += 1;
+  }
   const int nb = (nw_ub + kBlockW - 1) / kBlockW;
   const int nbe = nb + (nb & 1);
   unsigned long long* fl = h->prof ? h->d_prof_flops : nullptr;
@@ -300,6 +327,84 @@ int validate_layer(mps_state* h, int k, int ng, const int* sites, const void* Us
   return MPS_OK;
 }
 
+int oz_gemm(mps_state* h, int ng, int kind, int M_ub, int N_ub, int K_ub) {
+  launch_oz_jobs(h->d_tasks, h->d_meta, h->d_oz_jobs, ng, kind, h->stream);
+  const int ev = pbeg(h);
+  const int rc = ozaki_zgemm(h->d_oz_jobs, ng, M_ub, N_ub, K_ub, h->slices, h->oz_buf, h->d_oz_err, h->stream);
+  const int npair = h->slices * (h->slices + 1) / 2;
+  pend(h, 3, ev, 3, (double)ng * npair * 8.0 * M_ub * N_ub * K_ub);
+  h->launches_all += 1;
+  if (rc == -2) return fail(MPS_ERR_NOMEM, "split GEMM buffers");
+  if (rc) return fail(MPS_ERR_CUDA, "split GEMM launch failed");
+  return MPS_OK;
+}
+
+// Split-precision theta and SVD of a layer of two-site gates (split_path.cu):
+// theta by the split GEMM, fp32 preconditioning sweeps, Newton-Schulz
+// re-orthonormalisation of V and B = A V by the split GEMM, binary64 sweeps.
+int run_split_theta_svd(mps_state* h, int ng, int xl_ub, int x0_ub, int xr_ub, int nw_ub) {
+  if (!h->d_oz_jobs || h->oz_cap < h->task_cap) {
+    cudaFree(h->d_oz_jobs);
+    h->d_oz_jobs = nullptr;
+    CK(cudaMalloc(&h->d_oz_jobs, sizeof(OzJob) * h->task_cap));
+    h->oz_cap = h->task_cap;
+  }
+  if (!h->d_oz_err) {
+    CK(cudaMalloc(&h->d_oz_err, sizeof(int)));
+    CK(cudaMemset(h->d_oz_err, 0, sizeof(int)));
+  }
+  const int mw_ub = std::max(2 * xl_ub, 2 * xr_ub);
+  int rc = oz_gemm(h, ng, kOzTheta, 2 * xl_ub, 2 * xr_ub, x0_ub);
+  if (rc) return rc;
+  int ev = pbeg(h);
+  launch_gate_mix2(h->d_tasks, h->d_meta, ng, xl_ub, xr_ub, h->stream);
+  launch_frob(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub, 0, h->stream);
+  launch_to_f32(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub + (long long)nw_ub * nw_ub, h->stream);
+  pend(h, 5, ev, 3);
+  // fp32 preconditioning sweeps
+  const int nb = (nw_ub + kBlockW - 1) / kBlockW;
+  const int nbe = nb + (nb & 1);
+  unsigned long long* fl = h->prof ? h->d_prof_flops + 4 : nullptr;
+  for (int sw = 0; sw < kF32Sweeps; ++sw) {
+    for (int r = 0; r < nbe - 1; ++r) {
+      ev = pbeg(h);
+      launch_jacobi_round_f32(h->d_tasks, h->d_meta, ng, r, nbe / 2, fl, h->stream);
+      pend(h, 4, ev, 1);
+    }
+    CK(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
+    launch_sweep_end_nofail(h->d_meta, ng, kF32Sweeps, h->d_counter, h->stream);
+    h->launches_all += 1;
+    CK(cudaMemcpyAsync(h->h_counter, h->d_counter, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (*h->h_counter == 0) break;
+  }
+  ev = pbeg(h);
+  launch_v_to_f64(h->d_tasks, h->d_meta, ng, (long long)nw_ub * nw_ub, h->stream);
+  pend(h, 5, ev, 1);
+  for (int it = 0; it < 2; ++it) {  // Newton-Schulz: V <- V (3I - V^H V) / 2
+    rc = oz_gemm(h, ng, kOzVhV, nw_ub, nw_ub, nw_ub);
+    if (rc) return rc;
+    rc = oz_gemm(h, ng, kOzVP, nw_ub, nw_ub, nw_ub);
+    if (rc) return rc;
+    ev = pbeg(h);
+    launch_ns_update(h->d_tasks, h->d_meta, ng, (long long)nw_ub * nw_ub, h->stream);
+    pend(h, 5, ev, 1);
+  }
+  rc = oz_gemm(h, ng, kOzAV, mw_ub, nw_ub, nw_ub);
+  if (rc) return rc;
+  ev = pbeg(h);
+  launch_take_product(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub, h->stream);
+  pend(h, 5, ev, 1);
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, h->d_oz_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (err) {
+    CK(cudaMemset(h->d_oz_err, 0, sizeof(int)));
+    return fail(MPS_ERR_TIMEOUT, "split GEMM: a bounded wait ran out");
+  }
+  return run_svd(h, ng, nw_ub, 0, false);
+}
+
 // The update pipeline of one layer of k-site gates (k = 2, 3) whose gate
 // matrices are on the device at d_U + g * u_stride.
 int run_update(mps_state* h, int k, int ng, const int* sites, const double2* d_U, int u_stride) {
@@ -327,6 +432,10 @@ int run_update(mps_state* h, int k, int ng, const int* sites, const double2* d_U
     t.T = h->slots[g].T;
     t.sigma = h->slots[g].sigma;
     t.perm = h->slots[g].perm;
+    t.A32 = h->slots[g].A32;
+    t.V32 = h->slots[g].V32;
+    t.P = h->slots[g].P;
+    t.Q = h->slots[g].Q;
     h->h_tasks[g] = t;
     const int xl = h->ub[s], x0 = h->ub[s + 1], xr = h->ub[s + k];
     xl_ub = std::max(xl_ub, xl);
@@ -339,15 +448,22 @@ int run_update(mps_state* h, int k, int ng, const int* sites, const double2* d_U
   CK(cudaMemcpyAsync(h->d_tasks, h->h_tasks, sizeof(GateTask) * ng, cudaMemcpyHostToDevice, h->stream));
   launch_setup(h->d_tasks, h->d_meta, ng, 0, h->stream);
   h->launches_all += 1;
-  int ev = pbeg(h);
-  if (k == 2) launch_contract2(h->d_tasks, h->d_meta, ng, xl_ub, xr_ub, h->stream);
-  else launch_contract3(h->d_tasks, h->d_meta, ng, x0_ub, xl_ub, xr_ub, h->stream);
-  pend(h, 1, ev, k == 2 ? 1 : 2, fl_contract);
-  launch_frob(h->d_tasks, h->d_meta, ng, (long long)(2 * xl_ub) * ((k == 3 ? 4 : 2) * xr_ub), 0, h->stream);
-  h->launches_all += 1;
-  CK(cudaGetLastError());
-  int rc = run_svd(h, ng, nw_ub, 0);
-  if (rc) return rc;
+  int rc;
+  if (k == 2 && h->prec == MPS_PREC_SPLIT && h->cap <= kSplitMaxCap) {
+    rc = run_split_theta_svd(h, ng, xl_ub, x0_ub, xr_ub, nw_ub);
+    if (rc) return rc;
+  } else {
+    int ev = pbeg(h);
+    if (k == 2) launch_contract2(h->d_tasks, h->d_meta, ng, xl_ub, xr_ub, h->stream);
+    else launch_contract3(h->d_tasks, h->d_meta, ng, x0_ub, xl_ub, xr_ub, h->stream);
+    pend(h, 1, ev, k == 2 ? 1 : 2, fl_contract);
+    launch_frob(h->d_tasks, h->d_meta, ng, (long long)(2 * xl_ub) * ((k == 3 ? 4 : 2) * xr_ub), 0, h->stream);
+    h->launches_all += 1;
+    CK(cudaGetLastError());
+    rc = run_svd(h, ng, nw_ub, 0);
+    if (rc) return rc;
+  }
+  int ev;
   const int k_ub = std::min(h->cap, nw_ub);
   ev = pbeg(h);
   launch_colnorms(h->d_tasks, h->d_meta, ng, nw_ub, 0, h->stream);
@@ -631,7 +747,7 @@ int mps_set_mode(mps_handle h, int prec, int slices, int svd_mode) {
   if (prec != MPS_PREC_FP64 && prec != MPS_PREC_SPLIT) return fail(MPS_ERR_ARG, "unknown precision mode");
   if (slices != 0 && (slices < 3 || slices > 8)) return fail(MPS_ERR_ARG, "slices must be 0 or 3..8");
   if (svd_mode != 0) return fail(MPS_ERR_ARG, "svd_mode must be 0");
-  if (prec == MPS_PREC_SPLIT) return fail(MPS_ERR_ARG, "split precision is not built in this library");
+  CK(cudaStreamSynchronize(h->stream));
   h->prec = prec;
   h->slices = slices ? slices : 8;
   h->svd_mode = svd_mode;
@@ -661,12 +777,12 @@ int mps_apply_layer_device(mps_handle h, int k, int n_gates, const int* sites, c
 int mps_profile(mps_handle h, int enable) {
   if (!h) return fail(MPS_ERR_ARG, "NULL handle");
   CK(cudaStreamSynchronize(h->stream));
-  if (!h->d_prof_flops) CK(cudaMalloc(&h->d_prof_flops, 4 * sizeof(unsigned long long)));
-  CK(cudaMemset(h->d_prof_flops, 0, 4 * sizeof(unsigned long long)));
+  if (!h->d_prof_flops) CK(cudaMalloc(&h->d_prof_flops, kProfKinds * sizeof(unsigned long long)));
+  CK(cudaMemset(h->d_prof_flops, 0, kProfKinds * sizeof(unsigned long long)));
   h->prof = enable ? 1 : 0;
   h->ev_next = 0;
   h->prof_rec.clear();
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < kProfKinds; ++i) {
     h->prof_flops_host[i] = 0.0;
     h->prof_launch[i] = 0;
   }
@@ -676,7 +792,7 @@ int mps_profile(mps_handle h, int enable) {
 
 int mps_profile_read(mps_handle h, int kernel, double* ms, long long* launches, double* flops,
                      long long* launches_all) {
-  if (!h || kernel < 0 || kernel > 3) return fail(MPS_ERR_ARG, "bad arguments");
+  if (!h || kernel < 0 || kernel >= kProfKinds) return fail(MPS_ERR_ARG, "bad arguments");
   CK(cudaStreamSynchronize(h->stream));
   double tot = 0.0;
   for (const auto& r : h->prof_rec) {
@@ -685,7 +801,7 @@ int mps_profile_read(mps_handle h, int kernel, double* ms, long long* launches, 
     CK(cudaEventElapsedTime(&m, h->evs[r[1]], h->evs[r[2]]));
     tot += m;
   }
-  unsigned long long dev[4] = {0, 0, 0, 0};
+  unsigned long long dev[kProfKinds] = {0, 0, 0, 0, 0, 0};
   if (h->d_prof_flops) CK(cudaMemcpy(dev, h->d_prof_flops, sizeof(dev), cudaMemcpyDeviceToHost));
   if (ms) *ms = tot;
   if (launches) *launches = h->prof_launch[kernel];

@@ -40,6 +40,11 @@ struct GateTask {
   double2* T;           // [4][cap][cap] scratch (3-site partial contraction / second split)
   double* sigma;        // column norms
   int* perm;            // sorted column order
+  // split-precision workspace (MPS_PREC_SPLIT)
+  float2* A32;          // fp32 copy of the working matrix (preconditioning sweeps)
+  float2* V32;          // fp32 right rotations
+  double2* P;           // Nw x Nw scratch (V^H V, then V P)
+  double2* Q;
 };
 
 // Per-task state written and read by kernels only.

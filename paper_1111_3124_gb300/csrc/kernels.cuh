@@ -18,6 +18,9 @@ void launch_init_V(const GateTask* t, const TaskMeta* m, int ntask, int nw_ub, c
 void launch_jacobi_round(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub, int second,
                          unsigned long long* flops, cudaStream_t st);
 void launch_sweep_end(TaskMeta* m, int ntask, int max_sweeps, int* active_count, cudaStream_t st);
+void launch_sweep_end_nofail(TaskMeta* m, int ntask, int max_sweeps, int* active_count, cudaStream_t st);
+void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub,
+                             unsigned long long* flops, cudaStream_t st);
 void launch_colnorms(const GateTask* t, const TaskMeta* m, int ntask, int nw_ub, int second, cudaStream_t st);
 void launch_truncate(const GateTask* t, TaskMeta* m, int ntask, int stage, int chi_cap, cudaStream_t st);
 void launch_emit_left(const GateTask* t, const TaskMeta* m, int ntask, int r_ub, int k_ub, int stage,

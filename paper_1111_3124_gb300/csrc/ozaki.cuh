@@ -1,0 +1,55 @@
+// Split-precision (Ozaki scheme) complex GEMM on tcgen05 tensor cores.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace mpsgb {
+
+// A complex matrix view X(r, k), r < rows, k < K, element at
+//   p[(r / rb) * s_rb + (r % rb) * s_r + (k / kb) * s_kb + (k % kb) * s_k]
+// (rb = 0 or kb = 0: no blocking), optionally scaled by rscale[r % rb] and
+// kscale[k % kb] and conjugated. For the B operand the view is indexed
+// (n, k), i.e. it describes B^T.
+struct OzView {
+  const double2* p;
+  long long s_rb, s_r, s_kb, s_k;
+  int rb, kb;
+  const double* rscale;
+  const double* kscale;
+  int conj;
+};
+
+// One GEMM C = alpha * A B (A: M x K view a, B: K x N given as the N x K view
+// b); C is complex binary64, column-major: C[r + n * ldc].
+struct OzJob {
+  OzView a, b;
+  int M, N, K;
+  double2* C;
+  long long ldc;
+  double alpha;
+};
+
+// Device scratch for slices and scales, grown on demand by ozaki_zgemm.
+struct OzBuffers {
+  void* base = nullptr;
+  size_t bytes = 0;
+  static size_t bytes_needed(int jobs, int M_ub, int N_ub, int K_ub, int s);
+};
+
+// Runs njobs GEMMs (job table on the device; dims on the device, bounded by
+// M_ub, N_ub, K_ub) with s slices per operand. Returns 0 or a negative code.
+// Needs 2 K_ub <= 1024. d_err: device int set to 1 if a bounded wait ran out.
+int ozaki_zgemm(const OzJob* d_jobs, int njobs, int M_ub, int N_ub, int K_ub, int s, OzBuffers& buf, int* d_err,
+                cudaStream_t st);
+
+// Products of the split-precision two-site update (split_path.cu).
+enum { kOzTheta = 0, kOzVhV = 1, kOzVP = 2, kOzAV = 3 };
+struct GateTask;
+struct TaskMeta;
+void launch_oz_jobs(const GateTask* t, const TaskMeta* m, OzJob* jobs, int ntask, int kind, cudaStream_t st);
+void launch_gate_mix2(const GateTask* t, const TaskMeta* m, int ntask, int xl_ub, int xr_ub, cudaStream_t st);
+void launch_to_f32(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
+void launch_v_to_f64(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
+void launch_ns_update(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
+void launch_take_product(const GateTask* t, TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
+
+}  // namespace mpsgb

@@ -1,0 +1,467 @@
+// Split-precision complex GEMM on the 5th-generation tensor cores (sm_103a):
+// binary64-accurate C = A B from bf16 slice products accumulated in fp32
+// (the Ozaki scheme: Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012;
+// tensor-core form after Mukunoki et al., ISC 2020).
+//
+// Splitting. Each complex row r of A gets a power-of-two scale 2^{e_r} with
+// max_k |Re A_rk|, |Im A_rk| < 2^{e_r}; each entry is cut (truncated toward
+// zero) into s signed 7-bit digits, x = 2^{e_r} sum_{p=1..s} d_p 2^{-7p},
+// |d_p| <= 127, with integer arithmetic on the binary64 bit pattern. The same
+// for the columns of B (scales 2^{f_n}). A digit is exact in bf16.
+// Complex to real: row 2r of A^ is [Re A_r, -Im A_r], row 2r+1 is
+// [Im A_r, Re A_r]; row n of B^ (K-major) is [Re B_:n, Im B_:n]. Then
+// (A^ B^T)[2r][n] = Re C_rn and [2r+1][n] = Im C_rn.
+// Products. Every slice pair (p, q) with p + q <= s + 1 is one tcgen05.mma
+// chain over K into its own fp32 TMEM accumulator. Each product of digits is
+// below 2^14 and 2K <= 1024 terms keep every partial sum below 2^24, so the
+// fp32 accumulation is exact. The epilogue folds the pair results into two
+// 64-bit integers per output (diagonals p+q <= 5 and > 5, shifted), and
+// converts them to binary64 once, with the scales 2^{e_r + f_n}.
+// Pipeline. One CTA per 128 x 64 output tile of A^ B^T: warp 0 issues TMA
+// loads (SWIZZLE_128B, 4 stages), warp 1 issues the MMAs (M = 128, N = 64,
+// K = 16 per instruction) alternating between two TMEM accumulators, warps
+// 2..9 drain an accumulator while the next pair is being multiplied. Every
+// wait is bounded (%globaltimer); a timeout sets an error flag and the CTA
+// returns after releasing its TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "engine.cuh"
+#include "kernels.cuh"
+#include "ozaki.cuh"
+
+namespace mpsgb {
+
+// --------------------------------------------------------------- splitting ---
+
+__device__ __forceinline__ double2 oz_elem(const OzView& v, int r, int k) {
+  const long long ro = v.rb ? (long long)(r / v.rb) * v.s_rb + (long long)(r % v.rb) * v.s_r : (long long)r * v.s_r;
+  const long long ko = v.kb ? (long long)(k / v.kb) * v.s_kb + (long long)(k % v.kb) * v.s_k : (long long)k * v.s_k;
+  double2 x = v.p[ro + ko];
+  double sc = 1.0;
+  if (v.rscale) sc *= v.rscale[v.rb ? r % v.rb : r];
+  if (v.kscale) sc *= v.kscale[v.kb ? k % v.kb : k];
+  x.x *= sc;
+  x.y *= v.conj ? -sc : sc;
+  return x;
+}
+
+// Exponent e with |x| < 2^e for every x whose magnitude is at most mx (e = 0 for mx = 0).
+__device__ __forceinline__ int oz_exponent(double mx) {
+  if (!(mx > 0.0)) return 0;
+  const long long b = __double_as_longlong(mx);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0) return -1022;  // subnormal maximum: scale as the smallest normal
+  return E - 1022;           // mx < 2^{E-1023+1}
+}
+
+// Digits of x relative to 2^e: x ~ 2^e sum_{p=1..s} d_p 2^{-7p} (truncation toward zero).
+__device__ __forceinline__ void oz_digits(double x, int e, int s, int* d) {
+  const long long b = __double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  long long X = 0;
+  if (E != 0) {
+    const long long m = (b & 0x000FFFFFFFFFFFFFLL) | 0x0010000000000000LL;
+    const int sh = E - 1019 - e;  // X = |x| 2^{56-e} = m 2^{E-1075+56-e}
+    if (sh >= 0) X = m << sh;     // sh <= 3 because |x| < 2^e
+    else if (sh > -64) X = m >> (-sh);
+  }
+  const bool neg = b < 0;
+#pragma unroll
+  for (int p = 1; p <= 8; ++p) {
+    int v = (int)((X >> (56 - 7 * p)) & 127);
+    d[p - 1] = p <= s ? (neg ? -v : v) : 0;
+  }
+}
+
+// One warp per complex row of the view: scale, digits, K-padding zeros.
+// Writes rows 2r and 2r+1 of every slice of A^ ([slice][Mp][Kp] bf16).
+// mode 0: A operand (row 2r = [Re, -Im], 2r+1 = [Im, Re]);
+// mode 1: B operand (row r = [Re, Im]).
+__global__ void __launch_bounds__(256) k_oz_split(const OzJob* jobs, int which, __nv_bfloat16* out, int* expo,
+                                                  int Mp, int Kp, int s) {
+  const OzJob& jb = jobs[blockIdx.y];
+  const OzView& v = which == 0 ? jb.a : jb.b;
+  const int R = which == 0 ? jb.M : jb.N;
+  const int K = jb.K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + warp;
+  const int rows_out = which == 0 ? 2 : 1;
+  const int rows_cap = which == 0 ? Mp / 2 : Mp;
+  if (r >= rows_cap) return;
+  const size_t slice_stride = (size_t)Mp * Kp;
+  __nv_bfloat16* base = out + (size_t)blockIdx.y * s * slice_stride;
+  const int kpad = (2 * K + 63) & ~63;
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+  if (r >= R) {  // rows beyond R only feed outputs that are never written
+    if (lane == 0) expo[(size_t)blockIdx.y * rows_cap + r] = 0;
+    return;
+  }
+  double mx = 0.0;
+  for (int k = lane; k < K; k += 32) {
+    const double2 x = oz_elem(v, r, k);
+    mx = fmax(mx, fmax(fabs(x.x), fabs(x.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int e = oz_exponent(mx);
+  if (lane == 0) expo[(size_t)blockIdx.y * rows_cap + r] = e;
+  for (int k = lane; k < K; k += 32) {
+    const double2 x = oz_elem(v, r, k);
+    int dre[8], dim[8];
+    oz_digits(x.x, e, s, dre);
+    oz_digits(x.y, e, s, dim);
+    for (int p = 0; p < s; ++p) {
+      __nv_bfloat16* sl = base + p * slice_stride;
+      if (which == 0) {
+        sl[(size_t)(2 * r) * Kp + k] = __float2bfloat16_rn((float)dre[p]);
+        sl[(size_t)(2 * r) * Kp + K + k] = __float2bfloat16_rn((float)(-dim[p]));
+        sl[(size_t)(2 * r + 1) * Kp + k] = __float2bfloat16_rn((float)dim[p]);
+        sl[(size_t)(2 * r + 1) * Kp + K + k] = __float2bfloat16_rn((float)dre[p]);
+      } else {
+        sl[(size_t)r * Kp + k] = __float2bfloat16_rn((float)dre[p]);
+        sl[(size_t)r * Kp + K + k] = __float2bfloat16_rn((float)dim[p]);
+      }
+    }
+  }
+  for (int c = 2 * K + lane; c < kpad; c += 32)
+    for (int p = 0; p < s; ++p)
+      for (int ro = 0; ro < rows_out; ++ro) base[p * slice_stride + (size_t)(rows_out * r + ro) * Kp + c] = zero;
+}
+
+// ------------------------------------------------------------ PTX helpers ---
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: returns false after ~2 s without the phase completing.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (!mbar_try(bar, parity)) {
+    if (*(volatile int*)err) return false;
+    if (gtimer() - t0 > 2000000000ull) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, rows of 128 bytes, 128-byte
+// swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void* tile) {
+  const uint64_t addr = smem_u32(tile);
+  uint64_t d = 0;
+  d |= (addr & 0x3FFFFull) >> 4;        // start address
+  d |= (uint64_t)1 << 16;               // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+  d |= (uint64_t)1 << 46;               // descriptor version
+  d |= (uint64_t)2 << 61;               // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: bf16 A and B (K-major), fp32 D, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------------- GEMM ---
+
+constexpr int kOzM = 128, kOzN = 64, kOzK = 64, kOzStages = 4;
+constexpr int kOzABytes = kOzM * kOzK * 2, kOzBBytes = kOzN * kOzK * 2;
+constexpr int kOzThreads = 320;  // 10 warps
+constexpr int kOzSmem = kOzStages * (kOzABytes + kOzBBytes) + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int kOzTmemCols = 128;  // two 64-column fp32 accumulators
+
+__global__ void __launch_bounds__(kOzThreads, 1)
+    k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const OzJob* jobs,
+              const int* ea, const int* fb, int MpA, int NpB, int s, int* err) {
+  extern __shared__ __align__(1024) unsigned char oz_smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + kOzStages * kOzABytes;
+  uint64_t* bars = (uint64_t*)(sB + kOzStages * kOzBBytes);
+  uint64_t* full = bars;                 // [stages]
+  uint64_t* empty = bars + kOzStages;    // [stages]
+  uint64_t* accf = bars + 2 * kOzStages; // [2]
+  uint64_t* acce = accf + 2;             // [2]
+  uint32_t* tmem_slot = (uint32_t*)(acce + 2);
+
+  const OzJob& jb = jobs[blockIdx.z];
+  const int m0 = blockIdx.y * kOzM;  // rows of A^ (2 per complex row)
+  const int n0 = blockIdx.x * kOzN;
+  if (m0 >= 2 * jb.M || n0 >= jb.N || jb.K <= 0) return;  // uniform across the CTA
+  const int KT = (2 * jb.K + kOzK - 1) / kOzK;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kOzStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accf[i], 1);
+      mbar_init(&acce[i], 8);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kOzTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------------------------------------- TMA producer
+      int it = 0;
+      for (int p = 0; p < s; ++p)
+        for (int q = 0; p + q < s; ++q)
+          for (int kt = 0; kt < KT; ++kt, ++it) {
+            const int st = it % kOzStages;
+            const uint32_t ph = (uint32_t)(it / kOzStages) & 1u;
+            if (!mbar_wait(&empty[st], ph ^ 1u, err)) goto producer_done;
+            mbar_expect_tx(&full[st], kOzABytes + kOzBBytes);
+            tma_load_4d(sA + st * kOzABytes, &tmA, &full[st], kt * kOzK, m0, p, blockIdx.z);
+            tma_load_4d(sB + st * kOzBBytes, &tmB, &full[st], kt * kOzK, n0, q, blockIdx.z);
+          }
+    producer_done:;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---------------------------------------------- MMA issuer
+      const uint32_t idesc = idesc_bf16_f32(kOzM, kOzN);
+      int it = 0, pi = 0;
+      for (int p = 0; p < s; ++p)
+        for (int q = 0; p + q < s; ++q, ++pi) {
+          const int acc = pi & 1;
+          const uint32_t use = (uint32_t)(pi >> 1);
+          if (!mbar_wait(&acce[acc], (use & 1u) ^ 1u, err)) goto mma_done;
+          tc_fence_after();
+          const uint32_t dcol = tmem + (uint32_t)(acc * kOzN);
+          for (int kt = 0; kt < KT; ++kt, ++it) {
+            const int st = it % kOzStages;
+            const uint32_t ph = (uint32_t)(it / kOzStages) & 1u;
+            if (!mbar_wait(&full[st], ph, err)) goto mma_done;
+            tc_fence_after();
+            const uint64_t da = smem_desc_sw128(sA + st * kOzABytes);
+            const uint64_t db = smem_desc_sw128(sB + st * kOzBBytes);
+#pragma unroll
+            for (int kk = 0; kk < kOzK / 16; ++kk)
+              mma_bf16(dcol, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, (kt | kk) != 0);
+            mma_commit(&empty[st]);
+          }
+          mma_commit(&accf[acc]);
+        }
+    mma_done:;
+    }
+  } else {  // ----------------------------------------------------------- epilogue
+    const int quarter = warp & 3;
+    const int chalf = (warp - 2) >> 2;  // 0 or 1: columns [32 chalf, 32 chalf + 32)
+    const int dh = s < 5 ? s + 1 : 5;   // diagonals d = p+q (1-based) <= dh go to the high word
+    long long hi[32], lo[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      hi[j] = 0;
+      lo[j] = 0;
+    }
+    bool ok = true;
+    int pi = 0;
+    for (int p = 0; p < s && ok; ++p)
+      for (int q = 0; p + q < s; ++q, ++pi) {
+        const int acc = pi & 1;
+        const uint32_t use = (uint32_t)(pi >> 1);
+        if (!mbar_wait(&accf[acc], use & 1u, err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(acc * kOzN + 32 * chalf), v);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce[acc]);
+        const int d = p + q + 2;
+        if (d <= dh) {
+          const int sh = 7 * (dh - d);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) hi[j] += __float2ll_rn(v[j]) * (1LL << sh);
+        } else {
+          const int sh = 7 * (s + 1 - d);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) lo[j] += __float2ll_rn(v[j]) * (1LL << sh);
+        }
+      }
+    if (ok) {
+      const int m = m0 + 32 * quarter + lane;  // row of A^
+      if (m < 2 * jb.M) {
+        const int r = m >> 1, part = m & 1;
+        const int er = ea[(size_t)blockIdx.z * (MpA / 2) + r];
+        double* C = reinterpret_cast<double*>(jb.C);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + 32 * chalf + j;
+          if (n < jb.N) {
+            const int e = er + fb[(size_t)blockIdx.z * NpB + n];
+            const double val = ldexp((double)hi[j], e - 7 * dh) + ldexp((double)lo[j], e - 7 * (s + 1));
+            C[2 * ((size_t)r + (size_t)n * jb.ldc) + part] = jb.alpha * val;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kOzTmemCols));
+  }
+}
+
+// ------------------------------------------------------------ host side ---
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static int encode_fn() {
+  if (g_encode) return 0;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return -1;
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return 0;
+}
+
+// 4-D map over [jobs][slices][rows][Kp] bf16 with a (64 x box_rows) box.
+static int make_map(CUtensorMap* map, const __nv_bfloat16* base, int Kp, int rows, int s, int jobs, int box_rows) {
+  if (encode_fn()) return -1;
+  cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)s, (cuuint64_t)jobs};
+  cuuint64_t strides[3] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * rows * 2, (cuuint64_t)Kp * rows * s * 2};
+  cuuint32_t box[4] = {(cuuint32_t)kOzK, (cuuint32_t)box_rows, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(base), dims, strides, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+static inline int rup(int a, int b) { return (a + b - 1) / b * b; }
+
+size_t OzBuffers::bytes_needed(int jobs, int M_ub, int N_ub, int K_ub, int s) {
+  const size_t Mp = rup(2 * M_ub, kOzM), Np = rup(N_ub, kOzN), Kp = rup(2 * K_ub, kOzK);
+  return (size_t)jobs * s * (Mp + Np) * Kp * 2 + (size_t)jobs * (Mp / 2 + Np) * sizeof(int) + 4096;
+}
+
+int ozaki_zgemm(const OzJob* d_jobs, int njobs, int M_ub, int N_ub, int K_ub, int s, OzBuffers& buf, int* d_err,
+                cudaStream_t st) {
+  if (njobs <= 0) return 0;
+  if (s < 1 || s > 8 || 2 * K_ub > 1024) return -1;  // exact fp32 accumulation needs 2K <= 1024
+  const int Mp = rup(2 * M_ub, kOzM), Np = rup(N_ub, kOzN), Kp = rup(2 * K_ub, kOzK);
+  const size_t need = OzBuffers::bytes_needed(njobs, M_ub, N_ub, K_ub, s);
+  if (need > buf.bytes) {
+    cudaFree(buf.base);
+    buf.base = nullptr;
+    buf.bytes = 0;
+    if (cudaMalloc(&buf.base, need) != cudaSuccess) return -2;
+    buf.bytes = need;
+  }
+  unsigned char* p = static_cast<unsigned char*>(buf.base);
+  __nv_bfloat16* Ah = reinterpret_cast<__nv_bfloat16*>(p);
+  p += (size_t)njobs * s * Mp * Kp * 2;
+  __nv_bfloat16* Bh = reinterpret_cast<__nv_bfloat16*>(p);
+  p += (size_t)njobs * s * Np * Kp * 2;
+  int* ea = reinterpret_cast<int*>(p);
+  p += (size_t)njobs * (Mp / 2) * sizeof(int);
+  int* fb = reinterpret_cast<int*>(p);
+  k_oz_split<<<dim3((Mp / 2 + 7) / 8, njobs), 256, 0, st>>>(d_jobs, 0, Ah, ea, Mp, Kp, s);
+  k_oz_split<<<dim3((Np + 7) / 8, njobs), 256, 0, st>>>(d_jobs, 1, Bh, fb, Np, Kp, s);
+  CUtensorMap mA, mB;
+  if (make_map(&mA, Ah, Kp, Mp, s, njobs, kOzM) || make_map(&mB, Bh, Kp, Np, s, njobs, kOzN)) return -3;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem) != cudaSuccess) return -4;
+    attr = true;
+  }
+  k_oz_gemm<<<dim3(Np / kOzN, Mp / kOzM, njobs), kOzThreads, kOzSmem, st>>>(mA, mB, d_jobs, ea, fb, Mp, Np, s, d_err);
+  return cudaGetLastError() == cudaSuccess ? 0 : -5;
+}
+
+}  // namespace mpsgb

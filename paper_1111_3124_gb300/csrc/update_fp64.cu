@@ -243,9 +243,47 @@ __device__ __forceinline__ void rr_pair(int nbe, int r, int p, int& I, int& J) {
   }
 }
 
-template <int BW>
+// Complex type and unit roundoff of the arithmetic a Jacobi sweep runs in.
+template <typename R> struct Cx;
+template <> struct Cx<double> {
+  typedef double2 T;
+  static constexpr double eps = 1.1102230246251565e-16;  // 2^-53
+};
+template <> struct Cx<float> {
+  typedef float2 T;
+  static constexpr double eps = 5.9604644775390625e-08;  // 2^-24
+};
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ float2 cfma_cj(float2 a, float2 b, float2 acc) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+template <typename C, typename R> __device__ __forceinline__ C mkc(R x, R y);
+template <> __device__ __forceinline__ double2 mkc<double2, double>(double x, double y) { return make_double2(x, y); }
+template <> __device__ __forceinline__ float2 mkc<float2, float>(float x, float y) { return make_float2(x, y); }
+
+// One block pair (I, J) of a round: Gram of the 2b columns, Hermitian Jacobi
+// of the Gram, rotation of A's and V's columns. R = double: the binary64
+// sweep on (A, V) or (T, V); R = float: the fp32 preconditioning sweep on
+// (A32, V32). Rotation angles are computed in binary64 in both cases.
+template <int BW, typename R>
 __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, TaskMeta* meta, int round, int second,
                                                      unsigned long long* flops) {
+  typedef typename Cx<R>::T C;
+  constexpr double EPS = Cx<R>::eps;
   constexpr int C2 = 2 * BW;
   constexpr int NE = C2 * (C2 + 1) / 2;
   constexpr int RCH = 64;
@@ -261,13 +299,21 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   if (p >= nbe / 2) return;
   int I, J;
   rr_pair(nbe, round, p, I, J);
-  double2* A = work_A(tk, second);
-  double2* Vm = tk.V;
+  C* A;
+  C* Vm;
+  if constexpr (sizeof(R) == 8) {
+    A = work_A(tk, second);
+    Vm = tk.V;
+  } else {
+    A = tk.A32;
+    Vm = tk.V32;
+  }
+  const C zero = mkc<C, R>((R)0, (R)0);
 
   __shared__ int cols[C2];
-  __shared__ double2 chunk[RCH][C2 + 1];
-  __shared__ double2 G[C2][C2 + 1];
-  __shared__ double2 W[C2][C2 + 1];
+  __shared__ C chunk[RCH][C2 + 1];
+  __shared__ C G[C2][C2 + 1];
+  __shared__ C W[C2][C2 + 1];
   __shared__ double rc_c[C2 / 2], rc_t[C2 / 2], rc_g[C2 / 2], rc_a[C2 / 2], rc_b[C2 / 2];
   __shared__ double2 rc_se[C2 / 2];
   __shared__ int rc_on[C2 / 2];
@@ -292,12 +338,12 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   __syncthreads();
 
   // ---- Gram G = [A_I A_J]^H [A_I A_J]
-  double2 g = make_double2(0.0, 0.0);
+  C g = zero;
   for (int r0 = 0; r0 < Mw; r0 += RCH) {
     for (int e = tid; e < RCH * C2; e += 256) {
       const int col = e / RCH, row = e % RCH;
       const int gc = cols[col];
-      chunk[row][col] = (gc >= 0 && r0 + row < Mw) ? A[(size_t)(r0 + row) + (size_t)gc * Mw] : make_double2(0.0, 0.0);
+      chunk[row][col] = (gc >= 0 && r0 + row < Mw) ? A[(size_t)(r0 + row) + (size_t)gc * Mw] : zero;
     }
     __syncthreads();
     if (tid < NE) {
@@ -313,11 +359,11 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   __syncthreads();
   // ---- convergence test on the actual columns: |g_pq| <= Mw eps sqrt(g_pp g_qq),
   // numerically zero columns (g_jj <= (Mw eps)^2 ||A||_F^2) excluded
-  const double tolc = (double)Mw * kEps;
+  const double tolc = (double)Mw * EPS;
   const double tiny = tolc * tolc * mt.frob2;
   if (tid < NE && gp != gq) {
-    const double app = G[gp][gp].x, aqq = G[gq][gq].x;
-    const double gabs = hypot(g.x, g.y);
+    const double app = (double)G[gp][gp].x, aqq = (double)G[gq][gq].x;
+    const double gabs = hypot((double)g.x, (double)g.y);
     if (app > tiny && aqq > tiny && gabs > tolc * sqrt(app) * sqrt(aqq)) need = 1;
   }
   __syncthreads();
@@ -329,7 +375,7 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   }
 
   // ---- Hermitian Jacobi on G (two-sided, cyclic by circle-method rounds)
-  for (int e = tid; e < C2 * C2; e += 256) W[e / C2][e % C2] = make_double2((e / C2) == (e % C2) ? 1.0 : 0.0, 0.0);
+  for (int e = tid; e < C2 * C2; e += 256) W[e / C2][e % C2] = mkc<C, R>((e / C2) == (e % C2) ? (R)1 : (R)0, (R)0);
   __syncthreads();
   for (int isw = 0; isw < 24; ++isw) {
     if (tid == 0) any = 0;
@@ -338,14 +384,14 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
       if (tid < C2 / 2) {
         int pp, qq;
         rr_pair(C2, ir, tid, pp, qq);
-        const double al = G[pp][pp].x, be = G[qq][qq].x;
-        const double2 ga = G[pp][qq];
-        const double gabs = hypot(ga.x, ga.y);
-        int on = al > tiny && be > tiny && gabs > 0.0 && gabs > kEps * sqrt(al) * sqrt(be);
+        const double al = (double)G[pp][pp].x, be = (double)G[qq][qq].x;
+        const double gx = (double)G[pp][qq].x, gy = (double)G[pp][qq].y;
+        const double gabs = hypot(gx, gy);
+        int on = al > tiny && be > tiny && gabs > 0.0 && gabs > EPS * sqrt(al) * sqrt(be);
         rc_on[tid] = on;
         if (on) {
           // [al ga; conj(ga) be] = D [al g; g be] D^H, D = diag(1, e^{-i phi});
-          // real rotation of the middle matrix (Golub & Van Loan, sym.schur2)
+          // real rotation of the middle matrix (Golub & Van Loan, sym.schur2), in binary64
           const double zeta = (be - al) / (2.0 * gabs);
           double t = 1.0 / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           if (zeta < 0) t = -t;
@@ -356,7 +402,7 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
           rc_g[tid] = gabs;
           rc_a[tid] = al;
           rc_b[tid] = be;
-          rc_se[tid] = make_double2(s * ga.x / gabs, s * ga.y / gabs);  // s e^{i phi}
+          rc_se[tid] = make_double2(s * gx / gabs, s * gy / gabs);  // s e^{i phi}
           any = 1;
           atomicAdd(&nrot, 1);
         }
@@ -368,12 +414,12 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
         if (!rc_on[pr]) continue;
         int pp, qq;
         rr_pair(C2, ir, pr, pp, qq);
-        const double c = rc_c[pr];
-        const double2 se = rc_se[pr];
-        const double2 x = G[pp][col], y = G[qq][col];
-        const double2 sy = cmul(se, y), cx = cmul(cconj(se), x);
-        G[pp][col] = make_double2(c * x.x - sy.x, c * x.y - sy.y);
-        G[qq][col] = make_double2(cx.x + c * y.x, cx.y + c * y.y);
+        const R c = (R)rc_c[pr];
+        const C se = mkc<C, R>((R)rc_se[pr].x, (R)rc_se[pr].y);
+        const C x = G[pp][col], y = G[qq][col];
+        const C sy = cmul(se, y), cx = cmul(cconj(se), x);
+        G[pp][col] = mkc<C, R>(c * x.x - sy.x, c * x.y - sy.y);
+        G[qq][col] = mkc<C, R>(cx.x + c * y.x, cx.y + c * y.y);
       }
       __syncthreads();
       // columns: G <- G J and W <- W J (col p: c a_p - s e^{-i phi} a_q ; col q: s e^{i phi} a_p + c a_q)
@@ -384,22 +430,22 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
         if (!rc_on[pr]) continue;
         int pp, qq;
         rr_pair(C2, ir, pr, pp, qq);
-        double2(*Mx)[C2 + 1] = which ? W : G;
-        const double c = rc_c[pr];
-        const double2 se = rc_se[pr];
-        const double2 x = Mx[row][pp], y = Mx[row][qq];
-        const double2 sy = cmul(cconj(se), y), sx = cmul(se, x);
-        Mx[row][pp] = make_double2(c * x.x - sy.x, c * x.y - sy.y);
-        Mx[row][qq] = make_double2(sx.x + c * y.x, sx.y + c * y.y);
+        C(*Mx)[C2 + 1] = which ? W : G;
+        const R c = (R)rc_c[pr];
+        const C se = mkc<C, R>((R)rc_se[pr].x, (R)rc_se[pr].y);
+        const C x = Mx[row][pp], y = Mx[row][qq];
+        const C sy = cmul(cconj(se), y), sx = cmul(se, x);
+        Mx[row][pp] = mkc<C, R>(c * x.x - sy.x, c * x.y - sy.y);
+        Mx[row][qq] = mkc<C, R>(sx.x + c * y.x, sx.y + c * y.y);
       }
       __syncthreads();
       if (tid < C2 / 2 && rc_on[tid]) {
         int pp, qq;
         rr_pair(C2, ir, tid, pp, qq);
-        G[pp][qq] = make_double2(0.0, 0.0);
-        G[qq][pp] = make_double2(0.0, 0.0);
-        G[pp][pp] = make_double2(rc_a[tid] - rc_t[tid] * rc_g[tid], 0.0);
-        G[qq][qq] = make_double2(rc_b[tid] + rc_t[tid] * rc_g[tid], 0.0);
+        G[pp][qq] = zero;
+        G[qq][pp] = zero;
+        G[pp][pp] = mkc<C, R>((R)(rc_a[tid] - rc_t[tid] * rc_g[tid]), (R)0);
+        G[qq][qq] = mkc<C, R>((R)(rc_b[tid] + rc_t[tid] * rc_g[tid]), (R)0);
       }
       __syncthreads();
     }
@@ -410,20 +456,20 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
 
   // ---- rotate the columns of A (Mw rows) and of V (Nw rows) by W
   for (int pass = 0; pass < 2; ++pass) {
-    double2* Mx = pass == 0 ? A : Vm;
+    C* Mx = pass == 0 ? A : Vm;
     const int rows = pass == 0 ? Mw : Nw;
     for (int r0 = 0; r0 < rows; r0 += RCH) {
       for (int e = tid; e < RCH * C2; e += 256) {
         const int col = e / RCH, row = e % RCH;
         const int gc = cols[col];
-        chunk[row][col] = (gc >= 0 && r0 + row < rows) ? Mx[(size_t)(r0 + row) + (size_t)gc * rows] : make_double2(0.0, 0.0);
+        chunk[row][col] = (gc >= 0 && r0 + row < rows) ? Mx[(size_t)(r0 + row) + (size_t)gc * rows] : zero;
       }
       __syncthreads();
       for (int e = tid; e < RCH * C2; e += 256) {
         const int col = e / RCH, row = e % RCH;
         const int gc = cols[col];
         if (gc < 0 || r0 + row >= rows) continue;
-        double2 o = make_double2(0.0, 0.0);
+        C o = zero;
 #pragma unroll
         for (int k = 0; k < C2; ++k) o = cfma(chunk[row][k], W[k][col], o);
         Mx[(size_t)(r0 + row) + (size_t)gc * rows] = o;
@@ -433,14 +479,14 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   }
   if (tid == 0) {
     mt.rotated = 1;
-    // executed binary64 flops: Gram, inner rotations (rows/cols of G, cols of W), column rotations
+    // executed flops: Gram, inner rotations (rows/cols of G, cols of W), column rotations
     if (flops)
       atomicAdd(flops, 4ull * nv * (nv + 1) * (unsigned long long)Mw + 60ull * C2 * (unsigned long long)nrot +
                            8ull * nv * C2 * (unsigned long long)(Mw + Nw));
   }
 }
 
-__global__ void k_sweep_end(TaskMeta* meta, int ntask, int max_sweeps, int* active_count) {
+__global__ void k_sweep_end(TaskMeta* meta, int ntask, int max_sweeps, int* active_count, int fail_at_limit) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ntask) return;
   TaskMeta& m = meta[t];
@@ -451,8 +497,10 @@ __global__ void k_sweep_end(TaskMeta* meta, int ntask, int max_sweeps, int* acti
     m.active = 0;
   } else if (m.sweeps >= max_sweeps) {
     m.active = 0;
-    m.status = -4;                  // MPS_ERR_NOCONVERGE
-    atomicExch(active_count + 1, -4);  // sticky per-handle status word
+    if (fail_at_limit) {
+      m.status = -4;                     // MPS_ERR_NOCONVERGE
+      atomicExch(active_count + 1, -4);  // sticky per-handle status word
+    }
   } else {
     atomicAdd(active_count, 1);
   }
@@ -704,11 +752,20 @@ void launch_init_V(const GateTask* t, const TaskMeta* m, int ntask, int nw_ub, c
 
 void launch_jacobi_round(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub, int second,
                          unsigned long long* flops, cudaStream_t st) {
-  k_jacobi_pair<kBlockW><<<dim3(pairs_ub, ntask), 256, 0, st>>>(t, m, round, second, flops);
+  k_jacobi_pair<kBlockW, double><<<dim3(pairs_ub, ntask), 256, 0, st>>>(t, m, round, second, flops);
 }
 
 void launch_sweep_end(TaskMeta* m, int ntask, int max_sweeps, int* active_count, cudaStream_t st) {
-  k_sweep_end<<<cdiv(ntask, 128), 128, 0, st>>>(m, ntask, max_sweeps, active_count);
+  k_sweep_end<<<cdiv(ntask, 128), 128, 0, st>>>(m, ntask, max_sweeps, active_count, 1);
+}
+
+void launch_sweep_end_nofail(TaskMeta* m, int ntask, int max_sweeps, int* active_count, cudaStream_t st) {
+  k_sweep_end<<<cdiv(ntask, 128), 128, 0, st>>>(m, ntask, max_sweeps, active_count, 0);
+}
+
+void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub,
+                             unsigned long long* flops, cudaStream_t st) {
+  k_jacobi_pair<kBlockW, float><<<dim3(pairs_ub, ntask), 256, 0, st>>>(t, m, round, 0, flops);
 }
 
 void launch_colnorms(const GateTask* t, const TaskMeta* m, int ntask, int nw_ub, int second, cudaStream_t st) {

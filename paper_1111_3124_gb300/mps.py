@@ -30,7 +30,7 @@ EXPORTS = [
     "mps_create", "mps_destroy", "mps_set_stream", "mps_set_mode", "mps_reset", "mps_apply_gate",
     "mps_apply_layer", "mps_apply_layer_device", "mps_profile", "mps_profile_read", "mps_amplitude", "mps_amplitudes", "mps_expectation", "mps_reduced_density",
     "mps_get_schmidt", "mps_bond_dims", "mps_export", "mps_import", "mps_diag", "mps_sync", "mps_last_error",
-    "mps_gate2_update_noalloc",
+    "mps_gate2_update_noalloc", "mps_split_zgemm",
 ]
 
 
@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH):
         "mps_diag": [P, I, ip, ip, dp, ip],
         "mps_sync": [P],
         "mps_gate2_update_noalloc": [P, P, P, P, P, P, I, D, dp, P],
+        "mps_split_zgemm": [I, I, I, P, ctypes.c_longlong, P, ctypes.c_longlong, P, ctypes.c_longlong, I, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -290,3 +291,20 @@ def gate2_update_noalloc(gamma_l, gamma_r, lambda_l, lambda_m, lambda_r, chi, ch
         ctypes.c_void_p(lambda_l.data_ptr()), ctypes.c_void_p(lambda_m.data_ptr()),
         ctypes.c_void_p(lambda_r.data_ptr()), ctypes.c_void_p(chi.data_ptr()), chi_max, float(cutoff),
         _dp(U.view(np.float64)), ctypes.c_void_p(s) if s else None))
+
+
+def split_zgemm(A, B, slices: int = 8, stream=None):
+    """C = A @ B for CUDA complex128 torch tensors (2-D) by the split-precision
+    tensor-core GEMM. Returns a new tensor."""
+    import torch
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    At = A.t().contiguous()  # column-major A
+    Bt = B.t().contiguous()
+    Ct = torch.empty((N, M), dtype=torch.complex128, device=A.device)
+    s = getattr(stream, "cuda_stream", stream)
+    check(load_library().mps_split_zgemm(M, N, K, ctypes.c_void_p(At.data_ptr()), M, ctypes.c_void_p(Bt.data_ptr()),
+                                         K, ctypes.c_void_p(Ct.data_ptr()), M, slices,
+                                         ctypes.c_void_p(s) if s else None))
+    return Ct.t()

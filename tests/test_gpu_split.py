@@ -1,0 +1,128 @@
+"""The split-precision path (MPS_PREC_SPLIT) on the GPU, through the C ABI.
+
+1. The tcgen05 split GEMM against numpy's binary64 product: error relative to
+   |A||B| elementwise, per slice count, on random, ragged, zero and wide-
+   exponent inputs.
+2. Gate updates in split mode against the CPU oracle, with the tolerances of
+   the binary64 path (amplitudes 1e-10 absolute, spectra 1e-12 lambda_0,
+   reconstructed tensors 1e-11 of their largest entry).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.statevector import StateVector
+from paper_1111_3124_gb300 import circuits as C
+from tests.helpers import all_bits, oracle_run, random_state, spectrum_err, two_site_tensor
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    t.cuda.set_device(0)
+    from paper_1111_3124_gb300 import build as B
+    B.build()
+    return t
+
+
+def _gemm_err(torch, m, n, k, slices=8, scale=None, seed=0, zero_rows=False):
+    from paper_1111_3124_gb300.mps import split_zgemm
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, k)) + 1j * rng.standard_normal((m, k))
+    B = rng.standard_normal((k, n)) + 1j * rng.standard_normal((k, n))
+    if scale:
+        A *= (2.0 ** rng.integers(-scale, scale, size=m))[:, None]
+        B *= (2.0 ** rng.integers(-scale, scale, size=n))[None, :]
+    if zero_rows:
+        A[::3] = 0
+        B[:, 1::4] = 0
+    Cg = split_zgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), slices).cpu().numpy()
+    bound = np.abs(A) @ np.abs(B)
+    err = np.abs(Cg - A @ B)
+    if zero_rows:
+        assert np.all(Cg[::3] == 0) and np.all(Cg[:, 1::4] == 0)
+    return float(np.max(err / np.where(bound > 0, bound, 1.0)))
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (5, 3, 7), (64, 64, 64), (200, 130, 77), (129, 65, 300), (512, 512, 512)])
+def test_split_gemm_binary64_accuracy(torch, m, n, k):
+    assert _gemm_err(torch, m, n, k) < 4e-15
+
+
+def test_split_gemm_wide_exponents_and_zeros(torch):
+    assert _gemm_err(torch, 256, 200, 256, scale=40, seed=3) < 4e-15
+    assert _gemm_err(torch, 100, 90, 80, zero_rows=True, seed=5) < 4e-15
+
+
+def test_split_gemm_error_falls_with_slices(torch):
+    errs = [_gemm_err(torch, 150, 120, 100, slices=s, seed=9) for s in (2, 3, 4, 5, 6, 8)]
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[1] < 2e-5 and errs[3] < 2e-9
+
+
+def test_split_gemm_rejects_long_k(torch):
+    from paper_1111_3124_gb300.mps import MPSError, split_zgemm
+    with pytest.raises(MPSError):
+        split_zgemm(torch.zeros((4, 513), dtype=torch.complex128, device="cuda"),
+                    torch.zeros((513, 4), dtype=torch.complex128, device="cuda"))
+
+
+# ------------------------------------------------------------- split updates ---
+
+def split_mps(n, chi_max, cutoff):
+    from paper_1111_3124_gb300.mps import MPS, PREC_SPLIT
+    return MPS(n, chi_max, cutoff, PREC_SPLIT)
+
+
+def test_split_config1_all_amplitudes(torch):
+    c = C.CONFIGS[1]
+    n = c["n"]
+    layers = C.config_circuit(1)
+    g = split_mps(n, c["chi_max"], c["cutoff"])
+    g.run_layers(layers)
+    ref = oracle_run(n, layers, c["chi_max"], c["cutoff"])
+    sv = StateVector(n)
+    for layer in layers:
+        for site, U in layer:
+            sv.apply(list(range(site, site + {2: 1, 4: 2, 8: 3}[U.shape[0]])), U)
+    a = g.amplitudes(all_bits(n))
+    assert np.max(np.abs(a - sv.vector())) < 1e-10
+    for b in range(n - 1):
+        assert spectrum_err(g.schmidt(b), ref.schmidt(b)) < 1e-12
+
+
+def test_split_truncating_circuit_vs_oracle(torch):
+    n, chi_max, cutoff = 12, 8, 1e-12
+    layers = C.brickwork(n, 8, np.random.default_rng(55))
+    g = split_mps(n, chi_max, cutoff)
+    g.run_layers(layers)
+    ref = oracle_run(n, layers, chi_max, cutoff)
+    for b in range(n - 1):
+        assert spectrum_err(g.schmidt(b), ref.schmidt(b)) < 1e-12
+    bits = np.random.default_rng(1).integers(0, 2, size=(64, n)).astype(np.uint8)
+    assert np.max(np.abs(g.amplitudes(bits) - np.array([ref.amplitude(b) for b in bits]))) < 1e-10
+
+
+@pytest.mark.parametrize("chi,chi_max", [((1, 3, 5, 2, 1), 64), ((1, 37, 45, 29, 1), 64),
+                                         ((1, 70, 97, 50, 1), 128), ((1, 40, 40, 40, 1), 48),
+                                         ((1, 256, 256, 256, 1), 256)])
+def test_split_single_update_vs_oracle(torch, chi, chi_max):
+    n = len(chi) - 1
+    state = random_state(n, chi, sum(chi))
+    U = C.haar_unitary(4, np.random.default_rng(sum(chi) + 1))
+    ref = oracle.OracleMPS(n, chi_max, 1e-12)
+    ref.set_state(*state)
+    ref.apply_gate(1, U)
+    g = split_mps(n, chi_max, 1e-12)
+    g.import_state(*state)
+    g.apply_gate(1, U)
+    _, rg, rl = ref.get_state()
+    _, gg, gl = g.export()
+    assert len(gl[1]) == len(rl[1])
+    assert spectrum_err(gl[1], rl[1]) < 1e-12
+    tg, tr = two_site_tensor(gg, gl, 1), two_site_tensor(rg, rl, 1)
+    assert np.max(np.abs(tg - tr)) < 1e-11 * np.max(np.abs(tr))
