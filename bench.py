@@ -58,13 +58,23 @@ def args_parse():
     p.add_argument("--prec", default="fp64", choices=["fp64", "split"])
     p.add_argument("--cpu-sample", type=int, default=2, help="oracle updates timed for cpu_baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--n", type=int, default=None, help="override the qubit count (small profiling cases)")
+    p.add_argument("--depth", type=int, default=None, help="override the circuit depth")
     return p.parse_args()
+
+
+ARGS = None
 
 
 def workload():
     from paper_1111_3124_gb300 import circuits as C
-    c = C.CONFIGS[2]
-    layers = C.config_circuit(2)
+    c = dict(C.CONFIGS[2])
+    n = ARGS.n if ARGS and ARGS.n else c["n"]
+    depth = ARGS.depth if ARGS and ARGS.depth else c["depth"]
+    if (n, depth) != (c["n"], c["depth"]):
+        c["name"] = "n%d_d%d_u4_rz_chi%d" % (n, depth, c["chi_max"])
+    c["n"], c["depth"] = n, depth
+    layers = C.config_circuit(2, n=n, depth=depth)
     return c, layers, C.count_updates(layers)
 
 
@@ -313,7 +323,9 @@ def run_gpu(a):
 
 
 def main():
+    global ARGS
     a = args_parse()
+    ARGS = a
     if a.impl == "reference":
         import oracle
         oracle.build()

@@ -62,6 +62,7 @@ struct TaskMeta {
   double disc;          // discarded weight (summed over splits)
   double kept_norm;     // sqrt(sum of kept sigma^2) of the current split
   double frob2;         // ||A||_F^2 of the current working matrix
+  unsigned int maxoff;  // float bits: largest |g_pq|/sqrt(g_pp g_qq) seen in this sweep
 };
 
 // Readout / single-site tasks.

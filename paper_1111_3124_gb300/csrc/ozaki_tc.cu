@@ -240,6 +240,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Exact conversion of an integral fp32 value with |v| < 2^24 to int32 by
+// integer operations on its bit pattern (keeps the drain off the binary64 /
+// conversion pipe): v = m 2^(e-150) with m the 24-bit significand.
+__device__ __forceinline__ int f2i_exact(float v) {
+  const int b = __float_as_int(v);
+  const int e = (b >> 23) & 0xFF;
+  const int m = (b & 0x7FFFFF) | 0x800000;
+  const int sh = 150 - e;  // >= 0 because |v| < 2^24
+  const int mag = sh < 24 ? (m >> sh) : 0;
+  return b < 0 ? -mag : mag;
+}
+
 // ------------------------------------------------------------------- GEMM ---
 
 constexpr int kOzM = 128, kOzN = 64, kOzK = 64, kOzStages = 4;
@@ -362,11 +374,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         if (d <= dh) {
           const int sh = 7 * (dh - d);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) hi[j] += __float2ll_rn(v[j]) * (1LL << sh);
+          for (int j = 0; j < 32; ++j) hi[j] += (long long)f2i_exact(v[j]) * (1LL << sh);
         } else {
           const int sh = 7 * (s + 1 - d);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) lo[j] += __float2ll_rn(v[j]) * (1LL << sh);
+          for (int j = 0; j < 32; ++j) lo[j] += (long long)f2i_exact(v[j]) * (1LL << sh);
         }
       }
     if (ok) {

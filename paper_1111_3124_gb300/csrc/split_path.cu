@@ -179,6 +179,7 @@ __global__ void k_take_product(const GateTask* tasks, TaskMeta* meta) {
     mt.active = 1;
     mt.rotated = 0;
     mt.sweeps = 0;
+    mt.maxoff = 0u;
   }
 }
 

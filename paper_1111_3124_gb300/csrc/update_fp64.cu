@@ -84,6 +84,7 @@ __global__ void k_setup(const GateTask* tasks, TaskMeta* meta, int ntask, int st
   m.rotated = 0;
   m.sweeps = 0;
   m.frob2 = 0.0;
+  m.maxoff = 0u;
 }
 
 // ||A||_F^2 of every task's working matrix (invariant under the rotations).
@@ -359,14 +360,24 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   __syncthreads();
   // ---- convergence test on the actual columns: |g_pq| <= Mw eps sqrt(g_pp g_qq),
   // numerically zero columns (g_jj <= (Mw eps)^2 ||A||_F^2) excluded
-  const double tolc = (double)Mw * EPS;
-  const double tiny = tolc * tolc * mt.frob2;
+  // binary64: Mw eps, the test of the oracle; fp32 preconditioning: the noise
+  // floor of an fp32 Gram, 4 sqrt(Mw) eps_32
+  const double tolc = sizeof(R) == 8 ? (double)Mw * EPS : 4.0 * sqrt((double)Mw) * EPS;
+  const double tiny = (double)Mw * EPS * (double)Mw * EPS * mt.frob2;
+  __shared__ unsigned int smax;
+  if (tid == 0) smax = 0u;
+  __syncthreads();
   if (tid < NE && gp != gq) {
     const double app = (double)G[gp][gp].x, aqq = (double)G[gq][gq].x;
     const double gabs = hypot((double)g.x, (double)g.y);
-    if (app > tiny && aqq > tiny && gabs > tolc * sqrt(app) * sqrt(aqq)) need = 1;
+    if (app > tiny && aqq > tiny) {
+      const double ratio = gabs / (sqrt(app) * sqrt(aqq));
+      if (ratio > tolc) need = 1;
+      atomicMax(&smax, __float_as_uint((float)ratio));
+    }
   }
   __syncthreads();
+  if (tid == 0 && smax) atomicMax(&mt.maxoff, smax);
   int nv = 0;  // valid columns of this pair
   for (int c = 0; c < C2; ++c) nv += cols[c] >= 0;
   if (!need) {
@@ -486,14 +497,21 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   }
 }
 
-__global__ void k_sweep_end(TaskMeta* meta, int ntask, int max_sweeps, int* active_count, int fail_at_limit) {
+// End of a sweep: converged when no pair rotated, or (qstop > 0) when the
+// largest scaled off-diagonal met before rotation was below qstop: cyclic
+// Jacobi converges quadratically, so what remains after such a sweep is
+// O(n qstop^2), under the rotation threshold.
+__global__ void k_sweep_end(TaskMeta* meta, int ntask, int max_sweeps, int* active_count, int fail_at_limit,
+                            float qstop) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ntask) return;
   TaskMeta& m = meta[t];
   if (!m.active) return;
   m.sweeps += 1;
   m.sweeps_total += 1;
-  if (!m.rotated) {
+  const float maxoff = __uint_as_float(m.maxoff);
+  m.maxoff = 0u;
+  if (!m.rotated || (qstop > 0.f && maxoff < qstop)) {
     m.active = 0;
   } else if (m.sweeps >= max_sweeps) {
     m.active = 0;
@@ -756,11 +774,11 @@ void launch_jacobi_round(const GateTask* t, TaskMeta* m, int ntask, int round, i
 }
 
 void launch_sweep_end(TaskMeta* m, int ntask, int max_sweeps, int* active_count, cudaStream_t st) {
-  k_sweep_end<<<cdiv(ntask, 128), 128, 0, st>>>(m, ntask, max_sweeps, active_count, 1);
+  k_sweep_end<<<cdiv(ntask, 128), 128, 0, st>>>(m, ntask, max_sweeps, active_count, 1, kQuadStop);
 }
 
 void launch_sweep_end_nofail(TaskMeta* m, int ntask, int max_sweeps, int* active_count, cudaStream_t st) {
-  k_sweep_end<<<cdiv(ntask, 128), 128, 0, st>>>(m, ntask, max_sweeps, active_count, 0);
+  k_sweep_end<<<cdiv(ntask, 128), 128, 0, st>>>(m, ntask, max_sweeps, active_count, 0, 0.f);
 }
 
 void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub,
