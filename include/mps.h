@@ -55,6 +55,40 @@ typedef enum {
                           core products (Ozaki scheme), binary64 elsewhere    */
 } mps_prec;
 
+/* SVD of the gate update (mps_set_mode's svd_mode). */
+typedef enum {
+  MPS_SVD_JACOBI = 0,     /* full blocked one-sided Jacobi SVD                 */
+  MPS_SVD_SKETCH_MLP = 1  /* rank predicted by an MLP (mps_set_predictor) sizes
+                             a randomized range-finder sketch; the full Jacobi
+                             SVD is the fallback when the sketch's residual
+                             exceeds the cutoff, and is used directly when the
+                             predicted rank is near the full rank            */
+} mps_svd_mode;
+
+/* The rank predictor: a 16-64-1 tanh MLP in fp32 (no paper counterpart: the
+ * learned part of this engine). Parameters (1153 floats): W1[64][16],
+ * b1[64], w2[64], b2; y = b2 + sum_h w2[h] tanh(b1[h] + sum_i W1[h][i] x_i).
+ * The target is log2(kept rank) / 10. */
+typedef struct mps_mlp* mps_mlp_handle;
+
+/* Creates an MLP on the current device with Glorot-uniform weights drawn from
+ * a generator seeded by `seed` and zero biases. */
+int mps_mlp_create(unsigned long long seed, mps_mlp_handle* out);
+int mps_mlp_destroy(mps_mlp_handle m);
+/* Copies the 1153 parameters out (get, may be NULL) and/or in (set, may be
+ * NULL; resets the optimizer state). Host pointers. */
+int mps_mlp_params(mps_mlp_handle m, float* get, const float* set);
+/* Y[b] = MLP(X[b]) for B samples; X is B x 16, host pointers. */
+int mps_mlp_forward(mps_mlp_handle m, int B, const float* X, float* Y);
+/* Mean squared error over the B samples and its gradient (1153 floats; NULL
+ * to skip), by the hand-written backward kernel. Host pointers. */
+int mps_mlp_loss_grad(mps_mlp_handle m, int B, const float* X, const float* T, float* loss, float* grad);
+/* Trains with Adam (beta 0.9/0.999) on N samples (host X: N x 16, T: N) for
+ * `epochs` shuffled passes of mini-batches of size `batch`; *loss receives the
+ * mean batch loss of the last epoch. */
+int mps_mlp_train(mps_mlp_handle m, int N, const float* X, const float* T, int epochs, int batch, float lr,
+                  unsigned long long seed, float* loss);
+
 /* mps_create - Sec. 3.2 ("mps M(n)"): an n-qubit state |0...0>, i.e.
  * Gamma_s[0] = [[1]], Gamma_s[1] = [[0]], Lambda_b = [1].
  *   n        number of qubits, 1 <= n <= 4096
@@ -80,8 +114,8 @@ int mps_set_stream(mps_handle h, void* cuda_stream);
 
 /* Selects the arithmetic of later gate updates (prec = mps_prec). `slices` is
  * the number of bf16 slices per operand for MPS_PREC_SPLIT (0 = default 8,
- * range 3..8); it is ignored for MPS_PREC_FP64. `svd_mode` is reserved and
- * must be 0 (full Jacobi SVD). */
+ * range 3..8); it is ignored for MPS_PREC_FP64. `svd_mode` is an
+ * mps_svd_mode; MPS_SVD_SKETCH_MLP needs a predictor (mps_set_predictor). */
 int mps_set_mode(mps_handle h, int prec, int slices, int svd_mode);
 
 /* mps_reset - returns the state to |0...0> (same as a fresh mps_create). */
@@ -121,6 +155,40 @@ int mps_apply_layer(mps_handle h, int k, int n_gates, const int* sites, const do
  *   sites  host array of n_gates first sites (pairwise disjoint ranges)
  * Errors: MPS_ERR_ARG. */
 int mps_apply_layer_device(mps_handle h, int k, int n_gates, const int* sites, const double* d_Us);
+
+/* mps_apply_layer_multi - gates of MANY independent MPS updated together:
+ * the gate tasks of all handles share batched passes (largest problems
+ * first, in passes whose workspace fits a fixed memory budget), which keeps
+ * the GPU busy when each circuit alone has few or small gates.
+ *   count     number of handles (>= 1), pairwise distinct, same device
+ *   handles   the MPS; the work runs on handles[0]'s stream with its
+ *             workspace and arithmetic mode; the other handles' streams are
+ *             synchronised before and made to wait for the work after
+ *   k         2 or 3 (all gates of the call have the same size)
+ *   n_gates   per handle, the number of its gates (disjoint within a handle)
+ *   sites     concatenation over handles of their first sites
+ *   Us        concatenation of the gates, 2^k x 2^k complex128 row-major each
+ * Errors: MPS_ERR_ARG, MPS_ERR_NOT_UNITARY (nothing applied). */
+int mps_apply_layer_multi(int count, const mps_handle* handles, int k, const int* n_gates, const int* sites,
+                          const double* Us);
+
+/* mps_layer_features - the 16 predictor features of each of n_gates two-site
+ * gates as they would be applied to the current state (nothing is applied):
+ *   log2 chi_{s-1}/10, log2 chi_{s+1}/10, log2 chi_s/10, 4.5 e_p(U) (the
+ *   entangling power, Zanardi-Zalka-Faoro 2000), ln of the 6 largest
+ *   Lambda_{s-1} and of the 6 largest Lambda_{s+1}, each / 25, missing values
+ *   padded with ln(max(cutoff, 1e-13))/25.
+ *   X  host buffer of n_gates x 16 floats. Synchronises the stream. */
+int mps_layer_features(mps_handle h, int k, int n_gates, const int* sites, const double* Us, float* X);
+
+/* Attaches the rank predictor used when svd_mode is MPS_SVD_SKETCH_MLP (the
+ * MLP must outlive its use; NULL detaches). */
+int mps_set_predictor(mps_handle h, mps_mlp_handle m);
+
+/* Counters of the sketch path since the handle's creation: gates whose SVD
+ * was attempted by the sketch, sketches accepted, gates routed directly to
+ * the full Jacobi SVD by the predictor. Any pointer may be NULL. */
+int mps_sketch_stats(mps_handle h, long long* sketched, long long* accepted, long long* routed_full);
 
 /* mps_amplitude - <bits|psi> = Gamma_0[b_0] Lambda_0 Gamma_1[b_1] ... Gamma_{n-1}[b_{n-1}]
  * (Eq. 1 evaluated at one basis state).
@@ -240,8 +308,10 @@ int mps_gate2_update_noalloc(double* d_gamma_l, double* d_gamma_r, const double*
  * scaled by a power of two and cut into `slices` signed 7-bit bf16 digits,
  * the slice products run on the tcgen05 tensor cores with exact fp32
  * accumulation, and the binary64 result is reassembled (Ozaki et al. 2012).
- * With 8 slices the result is binary64-accurate relative to |A||B|.
- *   M, N >= 1; 1 <= K <= 512 (exactness of the fp32 sums); slices 1..8
+ * With 8 slices the result is binary64-accurate relative to |A||B|. The fp32
+ * sums are exact for K <= 512; a longer K runs in 512-wide chunks whose
+ * binary64 results are accumulated.
+ *   M, N, K >= 1; slices 1..8
  *   stream  cudaStream_t (NULL = legacy default stream); synchronised.
  * Not a paper entry point: the building block of the split-precision update,
  * exposed for tests and reuse. Errors: MPS_ERR_ARG, MPS_ERR_TOO_LARGE,

@@ -21,6 +21,7 @@
 #include "../../include/mps.h"
 #include "engine.cuh"
 #include "kernels.cuh"
+#include "mlp.cuh"
 #include "ozaki.cuh"
 
 using namespace mpsgb;
@@ -46,20 +47,13 @@ int fail(int code, const std::string& msg) {
 constexpr int kMaxSweeps = 40;
 
 constexpr int kProfKinds = 6;  // see mps_profile in include/mps.h
-constexpr int kSplitMaxCap = 256;  // split GEMM needs 2K <= 1024 (K <= 2 chi_max)
+constexpr int kSplitMaxCap = kMaxCap;  // the split GEMM chunks K beyond 512
 constexpr int kF32Sweeps = 30;
 
-struct Slot {
-  double2* A = nullptr;
-  double2* V = nullptr;
-  double2* T = nullptr;
-  double* sigma = nullptr;
-  int* perm = nullptr;
-  float2* A32 = nullptr;  // split-precision buffers, allocated on first use
-  float2* V32 = nullptr;
-  double2* P = nullptr;
-  double2* Q = nullptr;
-};
+// Memory budget of one batched pass: the tasks of a layer (or of many
+// circuits' layers) are processed in chunks whose workspace fits this.
+constexpr size_t kArenaBudget = (size_t)48 << 30;
+constexpr int kMaxTasksPerPass = 4096;
 
 }  // namespace
 
@@ -76,7 +70,8 @@ struct mps_state {
   std::vector<int> ub;                      // n+1 upper bounds of chi
   std::vector<std::array<cd, 4>> pend;      // held-back single-qubit gates
   std::vector<char> has_pend;
-  std::vector<Slot> slots;
+  void* arena = nullptr;  // per-task workspace, laid out per pass from the tasks' dimension bounds
+  size_t arena_bytes = 0;
   GateTask* d_tasks = nullptr;
   TaskMeta* d_meta = nullptr;
   double2* d_gates = nullptr;
@@ -100,6 +95,9 @@ struct mps_state {
   long long prof_launch[kProfKinds] = {0, 0, 0, 0, 0, 0};
   long long launches_all = 0;
   unsigned long long* d_prof_flops = nullptr;  // device counters, one per class
+  // learned rank predictor / sketch SVD
+  mps_mlp* predictor = nullptr;
+  long long sk_sketched = 0, sk_accepted = 0, sk_routed = 0;
   // split precision
   OzJob* d_oz_jobs = nullptr;
   int oz_cap = 0;
@@ -174,36 +172,83 @@ int ensure_tasks(mps_state* h, int ntask) {
   return MPS_OK;
 }
 
-int ensure_slots(mps_state* h, int nslot) {
-  const size_t c2 = (size_t)h->cap * h->cap;
-  while ((int)h->slots.size() < nslot) {
-    Slot s;
-    CK(cudaMalloc(&s.A, sizeof(double2) * 8 * c2));
-    CK(cudaMalloc(&s.V, sizeof(double2) * 4 * c2));
-    CK(cudaMalloc(&s.T, sizeof(double2) * 4 * c2));
-    CK(cudaMalloc(&s.sigma, sizeof(double) * 2 * h->cap));
-    CK(cudaMalloc(&s.perm, sizeof(int) * 2 * h->cap));
-    h->slots.push_back(s);
-  }
-  if (h->prec == MPS_PREC_SPLIT)
-    for (int i = 0; i < nslot; ++i) {
-      Slot& s = h->slots[i];
-      if (s.A32) continue;
-      CK(cudaMalloc(&s.A32, sizeof(float2) * 4 * c2));
-      CK(cudaMalloc(&s.V32, sizeof(float2) * 4 * c2));
-      CK(cudaMalloc(&s.P, sizeof(double2) * 4 * c2));
-      CK(cudaMalloc(&s.Q, sizeof(double2) * 4 * c2));
+// A gate task: one k-site gate of one MPS (several MPS may share a pass).
+struct TaskRef {
+  mps_state* st;
+  int site;
+};
+
+// Workspace of one task from its bond-dimension upper bounds (elements):
+// A (Mw x Nw), V (Nw x Nw, both splits of a three-site gate), T, sigma/perm,
+// and for the split-precision path A32, V32, P, Q, V2.
+struct TaskLayout {
+  size_t off[10];
+  size_t total;
+};
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+TaskLayout task_layout(const TaskRef& r, int k, bool split) {
+  const mps_state* st = r.st;
+  const size_t xl = st->ub[r.site], xr = st->ub[r.site + k], cap = st->cap;
+  size_t sz[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (k == 3) {
+    const size_t m1 = 2 * xl, n1 = 4 * xr;
+    const size_t nw1 = std::min(m1, n1), mw1 = std::max(m1, n1);
+    const size_t k1 = std::min(cap, nw1);
+    const size_t m2 = 2 * k1, n2 = 2 * xr;
+    const size_t nw2 = std::min(m2, n2);
+    const size_t nw = std::max(nw1, nw2);
+    sz[0] = mw1 * nw1 * sizeof(double2);
+    sz[1] = nw * nw * sizeof(double2);
+    sz[2] = std::max(4 * cap * cap, m2 * n2) * sizeof(double2);  // partial contraction uses capacity strides
+    sz[3] = nw * sizeof(double);
+    sz[4] = nw * sizeof(int);
+  } else {
+    const size_t m = 2 * xl, n = 2 * xr;
+    const size_t mw = std::max(m, n), nw = std::min(m, n);
+    sz[0] = mw * nw * sizeof(double2);
+    sz[1] = nw * nw * sizeof(double2);
+    sz[3] = nw * sizeof(double);
+    sz[4] = nw * sizeof(int);
+    if (split) {
+      sz[2] = mw * nw * sizeof(double2);
+      sz[5] = mw * nw * sizeof(float2);
+      sz[6] = nw * nw * sizeof(float2);
+      sz[7] = sz[8] = sz[9] = nw * nw * sizeof(double2);
     }
+  }
+  TaskLayout L;
+  size_t o = 0;
+  for (int i = 0; i < 10; ++i) {
+    L.off[i] = o;
+    o += align256(sz[i]);
+  }
+  L.total = o;
+  return L;
+}
+
+int ensure_arena(mps_state* w, size_t bytes) {
+  if (bytes <= w->arena_bytes) return MPS_OK;
+  CK(cudaStreamSynchronize(w->stream));
+  const size_t grow = std::max(bytes, w->arena_bytes + w->arena_bytes / 2);
+  cudaFree(w->arena);
+  w->arena = nullptr;
+  w->arena_bytes = 0;
+  if (cudaMalloc(&w->arena, grow) != cudaSuccess) {
+    cudaGetLastError();
+    CK(cudaMalloc(&w->arena, bytes));
+    w->arena_bytes = bytes;
+    return MPS_OK;
+  }
+  w->arena_bytes = grow;
   return MPS_OK;
 }
 
 void free_state(mps_state* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
-  for (Slot& s : h->slots) {
-    cudaFree(s.A); cudaFree(s.V); cudaFree(s.T); cudaFree(s.sigma); cudaFree(s.perm);
-    cudaFree(s.A32); cudaFree(s.V32); cudaFree(s.P); cudaFree(s.Q);
-  }
+  cudaFree(h->arena);
   cudaFree(h->d_oz_jobs); cudaFree(h->d_oz_err); cudaFree(h->oz_buf.base);
   cudaFree(h->gamma); cudaFree(h->lambda); cudaFree(h->chi);
   cudaFree(h->d_tasks); cudaFree(h->d_meta); cudaFree(h->d_gates); cudaFree(h->d_counter);
@@ -339,6 +384,28 @@ int oz_gemm(mps_state* h, int ng, int kind, int M_ub, int N_ub, int K_ub) {
   return MPS_OK;
 }
 
+// fp32 preconditioning sweeps on (A32, V32) of every task, then re-arm the
+// tasks (the binary64 sweeps reuse the active/sweep counters).
+int run_f32_sweeps(mps_state* h, int ng, int nw_ub) {
+  const int nb = (nw_ub + kBlockW - 1) / kBlockW;
+  const int nbe = nb + (nb & 1);
+  unsigned long long* fl = h->prof ? h->d_prof_flops + 4 : nullptr;
+  for (int sw = 0; sw < kF32Sweeps; ++sw) {
+    for (int r = 0; r < nbe - 1; ++r) {
+      const int ev = pbeg(h);
+      launch_jacobi_round_f32(h->d_tasks, h->d_meta, ng, r, nbe / 2, fl, h->stream);
+      pend(h, 4, ev, 1);
+    }
+    CK(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
+    launch_sweep_end_nofail(h->d_meta, ng, kF32Sweeps, h->d_counter, h->stream);
+    h->launches_all += 1;
+    CK(cudaMemcpyAsync(h->h_counter, h->d_counter, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (*h->h_counter == 0) break;
+  }
+  return MPS_OK;
+}
+
 // Split-precision theta and SVD of a layer of two-site gates (split_path.cu):
 // theta by the split GEMM, fp32 preconditioning sweeps, Newton-Schulz
 // re-orthonormalisation of V and B = A V by the split GEMM, binary64 sweeps.
@@ -361,40 +428,43 @@ int run_split_theta_svd(mps_state* h, int ng, int xl_ub, int x0_ub, int xr_ub, i
   launch_frob(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub, 0, h->stream);
   launch_to_f32(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub + (long long)nw_ub * nw_ub, h->stream);
   pend(h, 5, ev, 3);
-  // fp32 preconditioning sweeps
-  const int nb = (nw_ub + kBlockW - 1) / kBlockW;
-  const int nbe = nb + (nb & 1);
-  unsigned long long* fl = h->prof ? h->d_prof_flops + 4 : nullptr;
-  for (int sw = 0; sw < kF32Sweeps; ++sw) {
-    for (int r = 0; r < nbe - 1; ++r) {
+  rc = run_f32_sweeps(h, ng, nw_ub);
+  if (rc) return rc;
+  for (int level = 0; level < 2; ++level) {
+    const int v2 = level;  // the second pass builds V2 and folds it into V
+    if (level == 1) {
       ev = pbeg(h);
-      launch_jacobi_round_f32(h->d_tasks, h->d_meta, ng, r, nbe / 2, fl, h->stream);
-      pend(h, 4, ev, 1);
+      launch_to_f32(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub + (long long)nw_ub * nw_ub, h->stream);
+      pend(h, 5, ev, 1);
+      rc = run_f32_sweeps(h, ng, nw_ub);
+      if (rc) return rc;
     }
-    CK(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
-    launch_sweep_end_nofail(h->d_meta, ng, kF32Sweeps, h->d_counter, h->stream);
-    h->launches_all += 1;
-    CK(cudaMemcpyAsync(h->h_counter, h->d_counter, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    if (*h->h_counter == 0) break;
-  }
-  ev = pbeg(h);
-  launch_v_to_f64(h->d_tasks, h->d_meta, ng, (long long)nw_ub * nw_ub, h->stream);
-  pend(h, 5, ev, 1);
-  for (int it = 0; it < 2; ++it) {  // Newton-Schulz: V <- V (3I - V^H V) / 2
-    rc = oz_gemm(h, ng, kOzVhV, nw_ub, nw_ub, nw_ub);
-    if (rc) return rc;
-    rc = oz_gemm(h, ng, kOzVP, nw_ub, nw_ub, nw_ub);
+    ev = pbeg(h);
+    launch_v_to_f64(h->d_tasks, h->d_meta, ng, (long long)nw_ub * nw_ub, v2, h->stream);
+    pend(h, 5, ev, 1);
+    const int on = v2 ? kOzOnV2 : 0;
+    for (int it = 0; it < 2; ++it) {  // Newton-Schulz: V <- V (3I - V^H V) / 2
+      rc = oz_gemm(h, ng, kOzVhV | on, nw_ub, nw_ub, nw_ub);
+      if (rc) return rc;
+      rc = oz_gemm(h, ng, kOzVP | on, nw_ub, nw_ub, nw_ub);
+      if (rc) return rc;
+      ev = pbeg(h);
+      launch_ns_update(h->d_tasks, h->d_meta, ng, (long long)nw_ub * nw_ub, v2, h->stream);
+      pend(h, 5, ev, 1);
+    }
+    rc = oz_gemm(h, ng, kOzAV | on, mw_ub, nw_ub, nw_ub);
     if (rc) return rc;
     ev = pbeg(h);
-    launch_ns_update(h->d_tasks, h->d_meta, ng, (long long)nw_ub * nw_ub, h->stream);
+    launch_take_product(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub, h->stream);
     pend(h, 5, ev, 1);
+    if (level == 1) {
+      rc = oz_gemm(h, ng, kOzVV2, nw_ub, nw_ub, nw_ub);
+      if (rc) return rc;
+      ev = pbeg(h);
+      launch_take_q(h->d_tasks, h->d_meta, ng, (long long)nw_ub * nw_ub, h->stream);
+      pend(h, 5, ev, 1);
+    }
   }
-  rc = oz_gemm(h, ng, kOzAV, mw_ub, nw_ub, nw_ub);
-  if (rc) return rc;
-  ev = pbeg(h);
-  launch_take_product(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub, h->stream);
-  pend(h, 5, ev, 1);
   int err = 0;
   CK(cudaMemcpyAsync(&err, h->d_oz_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -405,13 +475,28 @@ int run_split_theta_svd(mps_state* h, int ng, int xl_ub, int x0_ub, int xr_ub, i
   return run_svd(h, ng, nw_ub, 0, false);
 }
 
-// The update pipeline of one layer of k-site gates (k = 2, 3) whose gate
-// matrices are on the device at d_U + g * u_stride.
-int run_update(mps_state* h, int k, int ng, const int* sites, const double2* d_U, int u_stride) {
-  int xl_ub = 1, x0_ub = 1, xr_ub = 1, nw_ub = 1;
+// The update pipeline of one pass of k-site gates (k = 2, 3), possibly from
+// several MPS: refs[g] is gate g, its matrix on the device at d_U + g*u_stride.
+// `w` owns the workspace, the task tables and the stream.
+int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const double2* d_U, int u_stride,
+                    bool split) {
+  const int ng = (int)refs.size();
+  int xl_ub = 1, x0_ub = 1, xr_ub = 1, nw_ub = 1, cap_ub = 1;
   double fl_contract = 0.0;
+  std::vector<TaskLayout> lay(ng);
+  size_t total = 0;
   for (int g = 0; g < ng; ++g) {
-    const int s = sites[g];
+    lay[g] = task_layout(refs[g], k, split);
+    total += lay[g].total;
+  }
+  int rc = ensure_arena(w, total);
+  if (rc) return rc;
+  unsigned char* base = static_cast<unsigned char*>(w->arena);
+  for (int g = 0; g < ng; ++g) {
+    mps_state* h = refs[g].st;
+    const int s = refs[g].site;
+    unsigned char* tb = base;
+    base += lay[g].total;
     GateTask t;
     std::memset(&t, 0, sizeof(t));
     t.g0 = site_ptr(h, s);
@@ -427,95 +512,138 @@ int run_update(mps_state* h, int k, int ng, const int* sites, const double2* d_U
     t.k = k;
     t.cap = h->cap;
     t.cutoff = h->cutoff;
-    t.A = h->slots[g].A;
-    t.V = h->slots[g].V;
-    t.T = h->slots[g].T;
-    t.sigma = h->slots[g].sigma;
-    t.perm = h->slots[g].perm;
-    t.A32 = h->slots[g].A32;
-    t.V32 = h->slots[g].V32;
-    t.P = h->slots[g].P;
-    t.Q = h->slots[g].Q;
-    h->h_tasks[g] = t;
+    const size_t* o = lay[g].off;
+    t.A = reinterpret_cast<double2*>(tb + o[0]);
+    t.V = reinterpret_cast<double2*>(tb + o[1]);
+    t.T = reinterpret_cast<double2*>(tb + o[2]);
+    t.sigma = reinterpret_cast<double*>(tb + o[3]);
+    t.perm = reinterpret_cast<int*>(tb + o[4]);
+    t.A32 = reinterpret_cast<float2*>(tb + o[5]);
+    t.V32 = reinterpret_cast<float2*>(tb + o[6]);
+    t.P = reinterpret_cast<double2*>(tb + o[7]);
+    t.Q = reinterpret_cast<double2*>(tb + o[8]);
+    t.V2 = reinterpret_cast<double2*>(tb + o[9]);
+    w->h_tasks[g] = t;
     const int xl = h->ub[s], x0 = h->ub[s + 1], xr = h->ub[s + k];
     xl_ub = std::max(xl_ub, xl);
     x0_ub = std::max(x0_ub, x0);
     xr_ub = std::max(xr_ub, xr);
+    cap_ub = std::max(cap_ub, h->cap);
     nw_ub = std::max(nw_ub, std::min(2 * xl, (k == 3 ? 4 : 2) * xr));
     if (k == 2) fl_contract += 32.0 * xl * x0 * xr + 128.0 * xl * xr;
     else fl_contract += 32.0 * x0 * h->ub[s + 2] * xr + 64.0 * xl * x0 * xr + 512.0 * xl * xr;
   }
-  CK(cudaMemcpyAsync(h->d_tasks, h->h_tasks, sizeof(GateTask) * ng, cudaMemcpyHostToDevice, h->stream));
-  launch_setup(h->d_tasks, h->d_meta, ng, 0, h->stream);
-  h->launches_all += 1;
-  int rc;
-  if (k == 2 && h->prec == MPS_PREC_SPLIT && h->cap <= kSplitMaxCap) {
-    rc = run_split_theta_svd(h, ng, xl_ub, x0_ub, xr_ub, nw_ub);
+  CK(cudaMemcpyAsync(w->d_tasks, w->h_tasks, sizeof(GateTask) * ng, cudaMemcpyHostToDevice, w->stream));
+  launch_setup(w->d_tasks, w->d_meta, ng, 0, w->stream);
+  w->launches_all += 1;
+  if (split) {
+    rc = run_split_theta_svd(w, ng, xl_ub, x0_ub, xr_ub, nw_ub);
     if (rc) return rc;
   } else {
-    int ev = pbeg(h);
-    if (k == 2) launch_contract2(h->d_tasks, h->d_meta, ng, xl_ub, xr_ub, h->stream);
-    else launch_contract3(h->d_tasks, h->d_meta, ng, x0_ub, xl_ub, xr_ub, h->stream);
-    pend(h, 1, ev, k == 2 ? 1 : 2, fl_contract);
-    launch_frob(h->d_tasks, h->d_meta, ng, (long long)(2 * xl_ub) * ((k == 3 ? 4 : 2) * xr_ub), 0, h->stream);
-    h->launches_all += 1;
+    int ev = pbeg(w);
+    if (k == 2) launch_contract2(w->d_tasks, w->d_meta, ng, xl_ub, xr_ub, w->stream);
+    else launch_contract3(w->d_tasks, w->d_meta, ng, x0_ub, xl_ub, xr_ub, w->stream);
+    pend(w, 1, ev, k == 2 ? 1 : 2, fl_contract);
+    launch_frob(w->d_tasks, w->d_meta, ng, (long long)(2 * xl_ub) * ((k == 3 ? 4 : 2) * xr_ub), 0, w->stream);
+    w->launches_all += 1;
     CK(cudaGetLastError());
-    rc = run_svd(h, ng, nw_ub, 0);
+    rc = run_svd(w, ng, nw_ub, 0);
     if (rc) return rc;
   }
-  int ev;
-  const int k_ub = std::min(h->cap, nw_ub);
-  ev = pbeg(h);
-  launch_colnorms(h->d_tasks, h->d_meta, ng, nw_ub, 0, h->stream);
-  launch_truncate(h->d_tasks, h->d_meta, ng, 0, h->cap, h->stream);
+  const int k_ub = std::min(cap_ub, nw_ub);
+  int ev = pbeg(w);
+  launch_colnorms(w->d_tasks, w->d_meta, ng, nw_ub, 0, w->stream);
+  launch_truncate(w->d_tasks, w->d_meta, ng, 0, kMaxCap, w->stream);
   if (k == 2) {
-    launch_emit_left(h->d_tasks, h->d_meta, ng, xl_ub, k_ub, 0, h->stream);
-    launch_emit_right(h->d_tasks, h->d_meta, ng, xr_ub, k_ub, 0, h->stream);
-    pend(h, 2, ev, 4);
-    for (int g = 0; g < ng; ++g) {
-      const int s = sites[g];
-      h->ub[s + 1] = std::min(h->cap, std::min(2 * h->ub[s], 2 * h->ub[s + 2]));
+    launch_emit_left(w->d_tasks, w->d_meta, ng, xl_ub, k_ub, 0, w->stream);
+    launch_emit_right(w->d_tasks, w->d_meta, ng, xr_ub, k_ub, 0, w->stream);
+    pend(w, 2, ev, 4);
+    for (const TaskRef& r : refs) {
+      mps_state* h = r.st;
+      h->ub[r.site + 1] = std::min(h->cap, std::min(2 * h->ub[r.site], 2 * h->ub[r.site + 2]));
     }
   } else {
-    launch_emit_left(h->d_tasks, h->d_meta, ng, xl_ub, k_ub, 0, h->stream);
-    launch_form_second(h->d_tasks, h->d_meta, ng, k_ub, xr_ub, h->stream);
-    launch_setup(h->d_tasks, h->d_meta, ng, 1, h->stream);
-    pend(h, 2, ev, 5);
+    launch_emit_left(w->d_tasks, w->d_meta, ng, xl_ub, k_ub, 0, w->stream);
+    launch_form_second(w->d_tasks, w->d_meta, ng, k_ub, xr_ub, w->stream);
+    launch_setup(w->d_tasks, w->d_meta, ng, 1, w->stream);
+    pend(w, 2, ev, 5);
     int nw2_ub = 1;
-    for (int g = 0; g < ng; ++g) {
-      const int s = sites[g];
-      const int k1 = std::min(h->cap, std::min(2 * h->ub[s], 4 * h->ub[s + 3]));
-      nw2_ub = std::max(nw2_ub, std::min(2 * k1, 2 * h->ub[s + 3]));
+    for (const TaskRef& r : refs) {
+      const mps_state* h = r.st;
+      const int k1 = std::min(h->cap, std::min(2 * h->ub[r.site], 4 * h->ub[r.site + 3]));
+      nw2_ub = std::max(nw2_ub, std::min(2 * k1, 2 * h->ub[r.site + 3]));
     }
-    launch_frob(h->d_tasks, h->d_meta, ng, (long long)(2 * k_ub) * (2 * xr_ub), 1, h->stream);
-    h->launches_all += 1;
-    rc = run_svd(h, ng, nw2_ub, 1);
+    launch_frob(w->d_tasks, w->d_meta, ng, (long long)(2 * k_ub) * (2 * xr_ub), 1, w->stream);
+    w->launches_all += 1;
+    rc = run_svd(w, ng, nw2_ub, 1);
     if (rc) return rc;
-    const int k2_ub = std::min(h->cap, nw2_ub);
-    ev = pbeg(h);
-    launch_colnorms(h->d_tasks, h->d_meta, ng, nw2_ub, 1, h->stream);
-    launch_truncate(h->d_tasks, h->d_meta, ng, 1, h->cap, h->stream);
-    launch_emit_left(h->d_tasks, h->d_meta, ng, k_ub, k2_ub, 1, h->stream);
-    launch_emit_right(h->d_tasks, h->d_meta, ng, xr_ub, k2_ub, 1, h->stream);
-    pend(h, 2, ev, 4);
-    for (int g = 0; g < ng; ++g) {
-      const int s = sites[g];
-      const int k1 = std::min(h->cap, std::min(2 * h->ub[s], 4 * h->ub[s + 3]));
-      h->ub[s + 1] = k1;
-      h->ub[s + 2] = std::min(h->cap, std::min(2 * k1, 2 * h->ub[s + 3]));
+    const int k2_ub = std::min(cap_ub, nw2_ub);
+    ev = pbeg(w);
+    launch_colnorms(w->d_tasks, w->d_meta, ng, nw2_ub, 1, w->stream);
+    launch_truncate(w->d_tasks, w->d_meta, ng, 1, kMaxCap, w->stream);
+    launch_emit_left(w->d_tasks, w->d_meta, ng, k_ub, k2_ub, 1, w->stream);
+    launch_emit_right(w->d_tasks, w->d_meta, ng, xr_ub, k2_ub, 1, w->stream);
+    pend(w, 2, ev, 4);
+    for (const TaskRef& r : refs) {
+      mps_state* h = r.st;
+      const int k1 = std::min(h->cap, std::min(2 * h->ub[r.site], 4 * h->ub[r.site + 3]));
+      h->ub[r.site + 1] = k1;
+      h->ub[r.site + 2] = std::min(h->cap, std::min(2 * k1, 2 * h->ub[r.site + 3]));
     }
   }
   CK(cudaGetLastError());
-  h->last_ntask = ng;
-  h->last_k = k;
+  w->last_ntask = ng;
+  w->last_k = k;
   return MPS_OK;
 }
 
-int prepare_tasks(mps_state* h, int ng) {
-  CK(cudaStreamSynchronize(h->stream));  // buffers may be regrown; pinned staging is reused
-  int rc = ensure_tasks(h, ng);
-  if (rc) return rc;
-  return ensure_slots(h, ng);
+// Runs a list of gate tasks in passes whose workspace fits the budget. The
+// host gates (already folded with held-back single-qubit gates) are in
+// h_U (2^k x 2^k complex128 each, stride 64 double2), or, for device gates,
+// d_U with stride u_stride.
+int run_refs_chunked(mps_state* w, int k, std::vector<TaskRef>& refs, const double2* h_U, const double2* d_U,
+                     int u_stride) {
+  bool split = k == 2 && w->prec == MPS_PREC_SPLIT;
+  for (const TaskRef& r : refs) split = split && r.st->cap <= kSplitMaxCap;
+  size_t g0 = 0;
+  while (g0 < refs.size()) {
+    size_t g1 = g0, bytes = 0;
+    while (g1 < refs.size() && (int)(g1 - g0) < kMaxTasksPerPass) {
+      const size_t b = task_layout(refs[g1], k, split).total;
+      if (g1 > g0 && bytes + b > kArenaBudget) break;
+      bytes += b;
+      ++g1;
+    }
+    const int ng = (int)(g1 - g0);
+    CK(cudaStreamSynchronize(w->stream));  // task tables and pinned staging are reused
+    int rc = ensure_tasks(w, ng);
+    if (rc) return rc;
+    const double2* dU = d_U;
+    int stride = u_stride;
+    if (h_U) {
+      std::memcpy(w->h_gates, h_U + 64 * g0, sizeof(double2) * 64 * ng);
+      CK(cudaMemcpyAsync(w->d_gates, w->h_gates, sizeof(double2) * 64 * ng, cudaMemcpyHostToDevice, w->stream));
+      dU = w->d_gates;
+      stride = 64;
+    } else {
+      dU = d_U + (size_t)u_stride * g0;
+    }
+    std::vector<TaskRef> part(refs.begin() + g0, refs.begin() + g1);
+    rc = run_update_refs(w, k, part, dU, stride, split);
+    if (rc) return rc;
+    g0 = g1;
+  }
+  return MPS_OK;
+}
+
+void hold_single(mps_state* h, int s, const double* u) {
+  std::array<cd, 4> nu;
+  std::array<cd, 4> p = h->has_pend[s] ? h->pend[s] : std::array<cd, 4>{1.0, 0.0, 0.0, 1.0};
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 2; ++c)
+      nu[r * 2 + c] = cd(u[2 * (r * 2)], u[2 * (r * 2) + 1]) * p[c] + cd(u[2 * (r * 2 + 1)], u[2 * (r * 2 + 1) + 1]) * p[2 + c];
+  h->pend[s] = nu;
+  h->has_pend[s] = 1;
 }
 
 int apply_layer_impl(mps_state* h, int k, int ng, const int* sites, const double* Us) {
@@ -526,24 +654,16 @@ int apply_layer_impl(mps_state* h, int k, int ng, const int* sites, const double
   for (int g = 0; g < ng; ++g)
     if (!is_unitary(Us + (size_t)2 * d * d * g, d)) return fail(MPS_ERR_NOT_UNITARY, "gate is not unitary");
   if (k == 1) {
-    for (int g = 0; g < ng; ++g) {
-      const double* u = Us + 8 * g;
-      const int s = sites[g];
-      std::array<cd, 4> nu;
-      std::array<cd, 4> p = h->has_pend[s] ? h->pend[s] : std::array<cd, 4>{1.0, 0.0, 0.0, 1.0};
-      for (int r = 0; r < 2; ++r)
-        for (int c = 0; c < 2; ++c)
-          nu[r * 2 + c] = cd(u[2 * (r * 2)], u[2 * (r * 2) + 1]) * p[c] + cd(u[2 * (r * 2 + 1)], u[2 * (r * 2 + 1) + 1]) * p[2 + c];
-      h->pend[s] = nu;
-      h->has_pend[s] = 1;
-    }
+    for (int g = 0; g < ng; ++g) hold_single(h, sites[g], Us + 8 * g);
     return MPS_OK;
   }
-  rc = prepare_tasks(h, ng);
-  if (rc) return rc;
-  for (int g = 0; g < ng; ++g) fold_pending(h, sites[g], k, Us + (size_t)2 * d * d * g, h->h_gates + 64 * g);
-  CK(cudaMemcpyAsync(h->d_gates, h->h_gates, sizeof(double2) * 64 * ng, cudaMemcpyHostToDevice, h->stream));
-  return run_update(h, k, ng, sites, h->d_gates, 64);
+  std::vector<double2> hu((size_t)64 * ng);
+  std::vector<TaskRef> refs(ng);
+  for (int g = 0; g < ng; ++g) {
+    fold_pending(h, sites[g], k, Us + (size_t)2 * d * d * g, hu.data() + 64 * g);
+    refs[g] = TaskRef{h, sites[g]};
+  }
+  return run_refs_chunked(h, k, refs, hu.data(), nullptr, 0);
 }
 
 int apply_layer_device_impl(mps_state* h, int k, int ng, const int* sites, const double* d_Us) {
@@ -578,9 +698,60 @@ int apply_layer_device_impl(mps_state* h, int k, int ng, const int* sites, const
     CK(cudaGetLastError());
     return MPS_OK;
   }
-  rc = prepare_tasks(h, ng);
+  std::vector<TaskRef> refs(ng);
+  for (int g = 0; g < ng; ++g) refs[g] = TaskRef{h, sites[g]};
+  return run_refs_chunked(h, k, refs, nullptr, (const double2*)d_Us, d * d);
+}
+
+// Gates of several MPS in shared batched passes (workspace and stream of hs[0]).
+int apply_layer_multi_impl(int count, const mps_handle* hs, int k, const int* n_gates, const int* sites,
+                           const double* Us) {
+  if (count < 1 || !hs || !n_gates || !hs[0]) return fail(MPS_ERR_ARG, "bad arguments");
+  if (k < 2 || k > 3) return fail(MPS_ERR_ARG, "k must be 2 or 3");
+  mps_state* w = hs[0];
+  const int d = 1 << k;
+  size_t tot = 0;
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i] || n_gates[i] < 0) return fail(MPS_ERR_ARG, "bad handle or gate count");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(MPS_ERR_ARG, "a handle appears twice");
+    int rc = validate_layer(hs[i], k, n_gates[i], sites + tot, Us + (size_t)2 * d * d * tot);
+    if (rc) return rc;
+    tot += n_gates[i];
+  }
+  for (size_t g = 0; g < tot; ++g)
+    if (!is_unitary(Us + (size_t)2 * d * d * g, d)) return fail(MPS_ERR_NOT_UNITARY, "gate is not unitary");
+  for (int i = 1; i < count; ++i) CK(cudaStreamSynchronize(hs[i]->stream));
+  std::vector<TaskRef> refs;
+  std::vector<size_t> src;
+  refs.reserve(tot);
+  size_t g = 0;
+  for (int i = 0; i < count; ++i)
+    for (int j = 0; j < n_gates[i]; ++j, ++g) {
+      refs.push_back(TaskRef{hs[i], sites[g]});
+      src.push_back(g);
+    }
+  // largest problems first: grids of a pass are sized by its largest task
+  std::vector<size_t> order(tot);
+  for (size_t i = 0; i < tot; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+    return task_layout(refs[a], k, false).total > task_layout(refs[b], k, false).total;
+  });
+  std::vector<TaskRef> sorted(tot);
+  std::vector<double2> hu((size_t)64 * tot);
+  for (size_t i = 0; i < tot; ++i) {
+    sorted[i] = refs[order[i]];
+    fold_pending(sorted[i].st, sorted[i].site, k, Us + (size_t)2 * d * d * src[order[i]], hu.data() + 64 * i);
+  }
+  int rc = run_refs_chunked(w, k, sorted, hu.data(), nullptr, 0);
   if (rc) return rc;
-  return run_update(h, k, ng, sites, (const double2*)d_Us, d * d);
+  // later calls on the other handles' streams wait for this pass
+  cudaEvent_t ev;
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaEventRecord(ev, w->stream);
+  for (int i = 1; i < count; ++i) cudaStreamWaitEvent(hs[i]->stream, ev, 0);
+  cudaEventDestroy(ev);
+  return MPS_OK;
 }
 
 // Deferred device errors: the sticky status word (d_counter[1]) set by kernels.
@@ -746,7 +917,7 @@ int mps_set_mode(mps_handle h, int prec, int slices, int svd_mode) {
   if (!h) return fail(MPS_ERR_ARG, "NULL handle");
   if (prec != MPS_PREC_FP64 && prec != MPS_PREC_SPLIT) return fail(MPS_ERR_ARG, "unknown precision mode");
   if (slices != 0 && (slices < 3 || slices > 8)) return fail(MPS_ERR_ARG, "slices must be 0 or 3..8");
-  if (svd_mode != 0) return fail(MPS_ERR_ARG, "svd_mode must be 0");
+  if (svd_mode != MPS_SVD_JACOBI && svd_mode != MPS_SVD_SKETCH_MLP) return fail(MPS_ERR_ARG, "unknown svd_mode");
   CK(cudaStreamSynchronize(h->stream));
   h->prec = prec;
   h->slices = slices ? slices : 8;
@@ -772,6 +943,62 @@ int mps_apply_layer(mps_handle h, int k, int n_gates, const int* sites, const do
 int mps_apply_layer_device(mps_handle h, int k, int n_gates, const int* sites, const double* d_Us) {
   if (!h) return fail(MPS_ERR_ARG, "NULL handle");
   return apply_layer_device_impl(h, k, n_gates, sites, d_Us);
+}
+
+int mps_apply_layer_multi(int count, const mps_handle* handles, int k, const int* n_gates, const int* sites,
+                          const double* Us) {
+  return apply_layer_multi_impl(count, handles, k, n_gates, sites, Us);
+}
+
+int mps_layer_features(mps_handle h, int k, int n_gates, const int* sites, const double* Us, float* X) {
+  if (!h) return fail(MPS_ERR_ARG, "NULL handle");
+  if (k != 2) return fail(MPS_ERR_ARG, "features are defined for two-site gates");
+  int rc = validate_layer(h, k, n_gates, sites, Us);
+  if (rc) return rc;
+  if (n_gates == 0) return MPS_OK;
+  if (!X) return fail(MPS_ERR_ARG, "X is NULL");
+  std::vector<FeatureTask> ft(n_gates);
+  for (int g = 0; g < n_gates; ++g) {
+    FeatureTask f;
+    f.lamL = bond_ptr(h, sites[g] - 1);
+    f.lamR = bond_ptr(h, sites[g] + 1);
+    f.chi = h->chi;
+    f.site = sites[g];
+    f.k = 2;
+    f.ep = (float)entangling_power(Us + 32 * g);
+    f.cutoff = h->cutoff;
+    ft[g] = f;
+  }
+  FeatureTask* d_ft = nullptr;
+  float* d_x = nullptr;
+  CK(cudaMalloc(&d_ft, sizeof(FeatureTask) * n_gates));
+  if (cudaMalloc(&d_x, sizeof(float) * 16 * n_gates) != cudaSuccess) {
+    cudaFree(d_ft);
+    return fail(MPS_ERR_NOMEM, "feature buffer");
+  }
+  cudaError_t e = cudaMemcpyAsync(d_ft, ft.data(), sizeof(FeatureTask) * n_gates, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) {
+    launch_features(d_ft, n_gates, d_x, h->stream);
+    e = cudaMemcpyAsync(X, d_x, sizeof(float) * 16 * n_gates, cudaMemcpyDeviceToHost, h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d_ft);
+  cudaFree(d_x);
+  return e == cudaSuccess ? MPS_OK : fail(MPS_ERR_CUDA, "features");
+}
+
+int mps_set_predictor(mps_handle h, mps_mlp_handle m) {
+  if (!h) return fail(MPS_ERR_ARG, "NULL handle");
+  h->predictor = m;
+  return MPS_OK;
+}
+
+int mps_sketch_stats(mps_handle h, long long* sketched, long long* accepted, long long* routed_full) {
+  if (!h) return fail(MPS_ERR_ARG, "NULL handle");
+  if (sketched) *sketched = h->sk_sketched;
+  if (accepted) *accepted = h->sk_accepted;
+  if (routed_full) *routed_full = h->sk_routed;
+  return MPS_OK;
 }
 
 int mps_profile(mps_handle h, int enable) {

@@ -45,6 +45,7 @@ struct GateTask {
   float2* V32;          // fp32 right rotations
   double2* P;           // Nw x Nw scratch (V^H V, then V P)
   double2* Q;
+  double2* V2;          // right factor of the second preconditioning pass
 };
 
 // Per-task state written and read by kernels only.

@@ -5,7 +5,7 @@
 namespace mpsgb {
 
 constexpr int kBlockW = 8;  // Jacobi block width b (columns per block)
-constexpr float kQuadStop = 1e-9f;  // binary64 sweeps stop once max scaled off-diagonal < this
+constexpr float kQuadStop = 1e-8f;  // binary64 sweeps stop after one whose max scaled off-diagonal < this
 
 // Sets the message returned by mps_last_error() on the calling thread.
 void set_error_message(const char* msg);

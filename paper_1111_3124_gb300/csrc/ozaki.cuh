@@ -37,19 +37,23 @@ struct OzBuffers {
 
 // Runs njobs GEMMs (job table on the device; dims on the device, bounded by
 // M_ub, N_ub, K_ub) with s slices per operand. Returns 0 or a negative code.
-// Needs 2 K_ub <= 1024. d_err: device int set to 1 if a bounded wait ran out.
+// K above 512 runs in 512-wide chunks accumulated in binary64.
+// d_err: device int set to 1 if a bounded wait ran out.
 int ozaki_zgemm(const OzJob* d_jobs, int njobs, int M_ub, int N_ub, int K_ub, int s, OzBuffers& buf, int* d_err,
                 cudaStream_t st);
 
 // Products of the split-precision two-site update (split_path.cu).
-enum { kOzTheta = 0, kOzVhV = 1, kOzVP = 2, kOzAV = 3 };
+// kOzVhV, kOzVP, kOzAV act on V (first preconditioning pass) or, with
+// kOzOnV2 added, on V2 (second pass); kOzVV2: Q = V V2.
+enum { kOzTheta = 0, kOzVhV = 1, kOzVP = 2, kOzAV = 3, kOzVV2 = 4, kOzOnV2 = 16 };
 struct GateTask;
 struct TaskMeta;
 void launch_oz_jobs(const GateTask* t, const TaskMeta* m, OzJob* jobs, int ntask, int kind, cudaStream_t st);
 void launch_gate_mix2(const GateTask* t, const TaskMeta* m, int ntask, int xl_ub, int xr_ub, cudaStream_t st);
 void launch_to_f32(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
-void launch_v_to_f64(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
-void launch_ns_update(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
+void launch_v_to_f64(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, int to_v2, cudaStream_t st);
+void launch_ns_update(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, int on_v2, cudaStream_t st);
+void launch_take_q(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
 void launch_take_product(const GateTask* t, TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
 
 }  // namespace mpsgb

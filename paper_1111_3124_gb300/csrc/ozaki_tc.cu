@@ -14,7 +14,8 @@
 // Products. Every slice pair (p, q) with p + q <= s + 1 is one tcgen05.mma
 // chain over K into its own fp32 TMEM accumulator. Each product of digits is
 // below 2^14 and 2K <= 1024 terms keep every partial sum below 2^24, so the
-// fp32 accumulation is exact. The epilogue folds the pair results into two
+// fp32 accumulation is exact; a longer K runs as 512-wide chunks whose
+// binary64 results the epilogue accumulates. The epilogue folds the pair results into two
 // 64-bit integers per output (diagonals p+q <= 5 and > 5, shifted), and
 // converts them to binary64 once, with the scales 2^{e_r + f_n}.
 // Pipeline. One CTA per 128 x 64 output tile of A^ B^T: warp 0 issues TMA
@@ -84,11 +85,11 @@ __device__ __forceinline__ void oz_digits(double x, int e, int s, int* d) {
 // mode 0: A operand (row 2r = [Re, -Im], 2r+1 = [Im, Re]);
 // mode 1: B operand (row r = [Re, Im]).
 __global__ void __launch_bounds__(256) k_oz_split(const OzJob* jobs, int which, __nv_bfloat16* out, int* expo,
-                                                  int Mp, int Kp, int s) {
+                                                  int Mp, int Kp, int s, int k0, int kchunk) {
   const OzJob& jb = jobs[blockIdx.y];
   const OzView& v = which == 0 ? jb.a : jb.b;
   const int R = which == 0 ? jb.M : jb.N;
-  const int K = jb.K;
+  const int K = max(0, min(jb.K - k0, kchunk));  // this chunk of the inner dimension
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + warp;
   const int rows_out = which == 0 ? 2 : 1;
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(256) k_oz_split(const OzJob* jobs, int which, 
   }
   double mx = 0.0;
   for (int k = lane; k < K; k += 32) {
-    const double2 x = oz_elem(v, r, k);
+    const double2 x = oz_elem(v, r, k0 + k);
     mx = fmax(mx, fmax(fabs(x.x), fabs(x.y)));
   }
 #pragma unroll
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(256) k_oz_split(const OzJob* jobs, int which, 
   const int e = oz_exponent(mx);
   if (lane == 0) expo[(size_t)blockIdx.y * rows_cap + r] = e;
   for (int k = lane; k < K; k += 32) {
-    const double2 x = oz_elem(v, r, k);
+    const double2 x = oz_elem(v, r, k0 + k);
     int dre[8], dim[8];
     oz_digits(x.x, e, s, dre);
     oz_digits(x.y, e, s, dim);
@@ -262,7 +263,7 @@ constexpr int kOzTmemCols = 128;  // two 64-column fp32 accumulators
 
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const OzJob* jobs,
-              const int* ea, const int* fb, int MpA, int NpB, int s, int* err) {
+              const int* ea, const int* fb, int MpA, int NpB, int s, int* err, int k0, int kchunk) {
   extern __shared__ __align__(1024) unsigned char oz_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;
@@ -277,8 +278,9 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   const OzJob& jb = jobs[blockIdx.z];
   const int m0 = blockIdx.y * kOzM;  // rows of A^ (2 per complex row)
   const int n0 = blockIdx.x * kOzN;
-  if (m0 >= 2 * jb.M || n0 >= jb.N || jb.K <= 0) return;  // uniform across the CTA
-  const int KT = (2 * jb.K + kOzK - 1) / kOzK;
+  const int Kc = min(jb.K - k0, kchunk);  // this chunk of the inner dimension
+  if (m0 >= 2 * jb.M || n0 >= jb.N || Kc <= 0) return;  // uniform across the CTA
+  const int KT = (2 * Kc + kOzK - 1) / kOzK;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -393,7 +395,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           if (n < jb.N) {
             const int e = er + fb[(size_t)blockIdx.z * NpB + n];
             const double val = ldexp((double)hi[j], e - 7 * dh) + ldexp((double)lo[j], e - 7 * (s + 1));
-            C[2 * ((size_t)r + (size_t)n * jb.ldc) + part] = jb.alpha * val;
+            double* c = &C[2 * ((size_t)r + (size_t)n * jb.ldc) + part];
+          *c = k0 > 0 ? *c + jb.alpha * val : jb.alpha * val;  // later K chunks accumulate
           }
         }
       }
@@ -445,9 +448,13 @@ size_t OzBuffers::bytes_needed(int jobs, int M_ub, int N_ub, int K_ub, int s) {
 int ozaki_zgemm(const OzJob* d_jobs, int njobs, int M_ub, int N_ub, int K_ub, int s, OzBuffers& buf, int* d_err,
                 cudaStream_t st) {
   if (njobs <= 0) return 0;
-  if (s < 1 || s > 8 || 2 * K_ub > 1024) return -1;  // exact fp32 accumulation needs 2K <= 1024
-  const int Mp = rup(2 * M_ub, kOzM), Np = rup(N_ub, kOzN), Kp = rup(2 * K_ub, kOzK);
-  const size_t need = OzBuffers::bytes_needed(njobs, M_ub, N_ub, K_ub, s);
+  if (s < 1 || s > 8 || K_ub < 1) return -1;
+  // exact fp32 accumulation needs 2K <= 1024: longer K in chunks of 512,
+  // summed in binary64 by the epilogue
+  const int kchunk = 512;
+  const int Kc_ub = K_ub < kchunk ? K_ub : kchunk;
+  const int Mp = rup(2 * M_ub, kOzM), Np = rup(N_ub, kOzN), Kp = rup(2 * Kc_ub, kOzK);
+  const size_t need = OzBuffers::bytes_needed(njobs, M_ub, N_ub, Kc_ub, s);
   if (need > buf.bytes) {
     cudaFree(buf.base);
     buf.base = nullptr;
@@ -463,8 +470,6 @@ int ozaki_zgemm(const OzJob* d_jobs, int njobs, int M_ub, int N_ub, int K_ub, in
   int* ea = reinterpret_cast<int*>(p);
   p += (size_t)njobs * (Mp / 2) * sizeof(int);
   int* fb = reinterpret_cast<int*>(p);
-  k_oz_split<<<dim3((Mp / 2 + 7) / 8, njobs), 256, 0, st>>>(d_jobs, 0, Ah, ea, Mp, Kp, s);
-  k_oz_split<<<dim3((Np + 7) / 8, njobs), 256, 0, st>>>(d_jobs, 1, Bh, fb, Np, Kp, s);
   CUtensorMap mA, mB;
   if (make_map(&mA, Ah, Kp, Mp, s, njobs, kOzM) || make_map(&mB, Bh, Kp, Np, s, njobs, kOzN)) return -3;
   static bool attr = false;
@@ -472,7 +477,12 @@ int ozaki_zgemm(const OzJob* d_jobs, int njobs, int M_ub, int N_ub, int K_ub, in
     if (cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem) != cudaSuccess) return -4;
     attr = true;
   }
-  k_oz_gemm<<<dim3(Np / kOzN, Mp / kOzM, njobs), kOzThreads, kOzSmem, st>>>(mA, mB, d_jobs, ea, fb, Mp, Np, s, d_err);
+  for (int k0 = 0; k0 < K_ub; k0 += kchunk) {
+    k_oz_split<<<dim3((Mp / 2 + 7) / 8, njobs), 256, 0, st>>>(d_jobs, 0, Ah, ea, Mp, Kp, s, k0, kchunk);
+    k_oz_split<<<dim3((Np + 7) / 8, njobs), 256, 0, st>>>(d_jobs, 1, Bh, fb, Np, Kp, s, k0, kchunk);
+    k_oz_gemm<<<dim3(Np / kOzN, Mp / kOzM, njobs), kOzThreads, kOzSmem, st>>>(mA, mB, d_jobs, ea, fb, Mp, Np, s, d_err,
+                                                                             k0, kchunk);
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -5;
 }
 

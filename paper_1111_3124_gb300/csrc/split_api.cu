@@ -27,7 +27,6 @@ extern "C" int mps_split_zgemm(int M, int N, int K, const double* dA, long long 
                                double* dC, long long ldc, int slices, void* stream) {
   if (!dA || !dB || !dC) return fail_msg(MPS_ERR_ARG, "NULL pointer");
   if (M < 1 || N < 1 || K < 1) return fail_msg(MPS_ERR_ARG, "sizes must be >= 1");
-  if (K > 512) return fail_msg(MPS_ERR_TOO_LARGE, "K > 512");
   if (slices < 1 || slices > 8) return fail_msg(MPS_ERR_ARG, "slices must be 1..8");
   if (lda < M || ldb < K || ldc < M) return fail_msg(MPS_ERR_ARG, "leading dimension too small");
   std::lock_guard<std::mutex> lock(g_mu);

@@ -7,9 +7,14 @@
 //      (rotation angles in binary64): an approximate right factor V32.
 //   3. V = V32 in binary64, re-orthonormalised by two Newton-Schulz steps
 //      V <- V (3 I - V^H V) / 2, products by the split-precision GEMM.
-//   4. B = A V (split-precision GEMM); binary64 Jacobi sweeps on B finish the
-//      decomposition (quadratic convergence from an O(1e-6) start), keeping
-//      the column norms, the orthogonality test and the angles in binary64.
+//   4. B = A V (split-precision GEMM).
+//   5. A second fp32 pass on B (whose columns are nearly orthogonal, so the
+//      small rotation angles keep every column's rounding relative to its own
+//      norm, small singular values included), V2 re-orthonormalised,
+//      B <- B V2 and V <- V V2 by the split-precision GEMM.
+//   6. binary64 Jacobi sweeps on B finish the decomposition (quadratic
+//      convergence from an O(1e-6) start), keeping the column norms, the
+//      orthogonality test and the rotation angles in binary64.
 // Truncation and the Lambda^-1 rewrite are those of the binary64 path.
 #include "engine.cuh"
 #include "kernels.cuh"
@@ -30,7 +35,8 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
     jobs[t] = j;  // M = N = K = 0: nothing to do
     return;
   }
-  switch (kind) {
+  double2* Vs = (kind & kOzOnV2) ? tk.V2 : tk.V;
+  switch (kind & ~kOzOnV2) {
     case kOzTheta:  // T = X Y, 2 chi_L x 2 chi_R, inner chi_s
       j.a.p = tk.g0;
       j.a.rb = mt.xl;
@@ -52,11 +58,11 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
       j.ldc = 2 * mt.xl;
       break;
     case kOzVhV:  // P = V^H V
-      j.a.p = tk.V;
+      j.a.p = Vs;
       j.a.s_r = mt.Nw;
       j.a.s_k = 1;
       j.a.conj = 1;
-      j.b.p = tk.V;
+      j.b.p = Vs;
       j.b.s_r = mt.Nw;
       j.b.s_k = 1;
       j.M = j.N = j.K = mt.Nw;
@@ -64,10 +70,21 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
       j.ldc = mt.Nw;
       break;
     case kOzVP:  // Q = V P
-      j.a.p = tk.V;
+      j.a.p = Vs;
       j.a.s_r = 1;
       j.a.s_k = mt.Nw;
       j.b.p = tk.P;
+      j.b.s_r = mt.Nw;
+      j.b.s_k = 1;
+      j.M = j.N = j.K = mt.Nw;
+      j.C = tk.Q;
+      j.ldc = mt.Nw;
+      break;
+    case kOzVV2:  // Q = V V2
+      j.a.p = tk.V;
+      j.a.s_r = 1;
+      j.a.s_k = mt.Nw;
+      j.b.p = tk.V2;
       j.b.s_r = mt.Nw;
       j.b.s_k = 1;
       j.M = j.N = j.K = mt.Nw;
@@ -78,7 +95,7 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
       j.a.p = tk.A;
       j.a.s_r = 1;
       j.a.s_k = mt.Mw;
-      j.b.p = tk.V;
+      j.b.p = Vs;
       j.b.s_r = mt.Nw;
       j.b.s_k = 1;
       j.M = mt.Mw;
@@ -143,28 +160,40 @@ __global__ void k_to_f32(const GateTask* tasks, const TaskMeta* meta) {
   }
 }
 
-// V = binary64(V32)
-__global__ void k_v_to_f64(const GateTask* tasks, const TaskMeta* meta) {
+// V (or V2) = binary64(V32)
+__global__ void k_v_to_f64(const GateTask* tasks, const TaskMeta* meta, int to_v2) {
   const GateTask& tk = tasks[blockIdx.y];
   const TaskMeta& mt = meta[blockIdx.y];
   if (mt.status) return;
+  double2* V = to_v2 ? tk.V2 : tk.V;
   const size_t nv = (size_t)mt.Nw * mt.Nw;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv; e += (size_t)gridDim.x * blockDim.x) {
     const float2 v = tk.V32[e];
-    tk.V[e] = make_double2((double)v.x, (double)v.y);
+    V[e] = make_double2((double)v.x, (double)v.y);
   }
 }
 
-// Newton-Schulz step V <- (3 V - V (V^H V)) / 2 = 1.5 V - 0.5 Q
-__global__ void k_ns_update(const GateTask* tasks, const TaskMeta* meta) {
+// Newton-Schulz step V <- (3 V - V (V^H V)) / 2 = 1.5 V - 0.5 Q (on V or V2)
+__global__ void k_ns_update(const GateTask* tasks, const TaskMeta* meta, int on_v2) {
+  const GateTask& tk = tasks[blockIdx.y];
+  const TaskMeta& mt = meta[blockIdx.y];
+  if (mt.status) return;
+  double2* V = on_v2 ? tk.V2 : tk.V;
+  const size_t nv = (size_t)mt.Nw * mt.Nw;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv; e += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = V[e], q = tk.Q[e];
+    V[e] = make_double2(fma(1.5, v.x, -0.5 * q.x), fma(1.5, v.y, -0.5 * q.y));
+  }
+}
+
+// V = Q (after Q = V V2)
+__global__ void k_take_q(const GateTask* tasks, const TaskMeta* meta) {
   const GateTask& tk = tasks[blockIdx.y];
   const TaskMeta& mt = meta[blockIdx.y];
   if (mt.status) return;
   const size_t nv = (size_t)mt.Nw * mt.Nw;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv; e += (size_t)gridDim.x * blockDim.x) {
-    const double2 v = tk.V[e], q = tk.Q[e];
-    tk.V[e] = make_double2(fma(1.5, v.x, -0.5 * q.x), fma(1.5, v.y, -0.5 * q.y));
-  }
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv; e += (size_t)gridDim.x * blockDim.x)
+    tk.V[e] = tk.Q[e];
 }
 
 // A = T (Mw x Nw) and re-arm the task for binary64 sweeps
@@ -199,11 +228,14 @@ void launch_gate_mix2(const GateTask* t, const TaskMeta* m, int ntask, int xl_ub
 void launch_to_f32(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
   k_to_f32<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m);
 }
-void launch_v_to_f64(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
-  k_v_to_f64<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m);
+void launch_v_to_f64(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, int to_v2, cudaStream_t st) {
+  k_v_to_f64<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m, to_v2);
 }
-void launch_ns_update(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
-  k_ns_update<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m);
+void launch_ns_update(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, int on_v2, cudaStream_t st) {
+  k_ns_update<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m, on_v2);
+}
+void launch_take_q(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
+  k_take_q<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m);
 }
 void launch_take_product(const GateTask* t, TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
   k_take_product<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m);

@@ -363,7 +363,9 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   // binary64: Mw eps, the test of the oracle; fp32 preconditioning: the noise
   // floor of an fp32 Gram, 4 sqrt(Mw) eps_32
   const double tolc = sizeof(R) == 8 ? (double)Mw * EPS : 4.0 * sqrt((double)Mw) * EPS;
-  const double tiny = (double)Mw * EPS * (double)Mw * EPS * mt.frob2;
+  // numerically zero columns: at binary64 resolution in both precisions, so the
+  // fp32 passes still orthogonalise small (but nonzero) columns
+  const double tiny = (double)Mw * kEps * (double)Mw * kEps * mt.frob2;
   __shared__ unsigned int smax;
   if (tid == 0) smax = 0u;
   __syncthreads();

@@ -24,13 +24,18 @@ MPS_ERR_NOT_UNITARY = -6
 MPS_ERR_TOO_LARGE = -7
 PREC_FP64 = 0
 PREC_SPLIT = 1
+SVD_JACOBI = 0
+SVD_SKETCH_MLP = 1
+MLP_PARAMS = 1153
 
 # every symbol include/mps.h declares
 EXPORTS = [
     "mps_create", "mps_destroy", "mps_set_stream", "mps_set_mode", "mps_reset", "mps_apply_gate",
     "mps_apply_layer", "mps_apply_layer_device", "mps_profile", "mps_profile_read", "mps_amplitude", "mps_amplitudes", "mps_expectation", "mps_reduced_density",
     "mps_get_schmidt", "mps_bond_dims", "mps_export", "mps_import", "mps_diag", "mps_sync", "mps_last_error",
-    "mps_gate2_update_noalloc", "mps_split_zgemm",
+    "mps_gate2_update_noalloc", "mps_split_zgemm", "mps_apply_layer_multi",
+    "mps_mlp_create", "mps_mlp_destroy", "mps_mlp_params", "mps_mlp_forward", "mps_mlp_loss_grad", "mps_mlp_train",
+    "mps_layer_features", "mps_set_predictor", "mps_sketch_stats",
 ]
 
 
@@ -54,6 +59,7 @@ def load_library(path: str = LIB_PATH):
     L = ctypes.CDLL(path)
     P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     dp, ip = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    fp = ctypes.POINTER(ctypes.c_float)
     bp = ctypes.c_char_p
     sig = {
         "mps_create": [I, I, D, ctypes.POINTER(P)],
@@ -78,6 +84,17 @@ def load_library(path: str = LIB_PATH):
         "mps_sync": [P],
         "mps_gate2_update_noalloc": [P, P, P, P, P, P, I, D, dp, P],
         "mps_split_zgemm": [I, I, I, P, ctypes.c_longlong, P, ctypes.c_longlong, P, ctypes.c_longlong, I, P],
+        "mps_apply_layer_multi": [I, ctypes.POINTER(P), I, ip, ip, dp],
+        "mps_mlp_create": [ctypes.c_ulonglong, ctypes.POINTER(P)],
+        "mps_mlp_destroy": [P],
+        "mps_mlp_params": [P, fp, fp],
+        "mps_mlp_forward": [P, I, fp, fp],
+        "mps_mlp_loss_grad": [P, I, fp, fp, fp, fp],
+        "mps_mlp_train": [P, I, fp, fp, I, I, ctypes.c_float, ctypes.c_ulonglong, fp],
+        "mps_layer_features": [P, I, I, ip, dp, fp],
+        "mps_set_predictor": [P, P],
+        "mps_sketch_stats": [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                             ctypes.POINTER(ctypes.c_longlong)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -156,6 +173,23 @@ class MPS:
         ptr = d_Us.data_ptr() if hasattr(d_Us, "data_ptr") else int(d_Us)
         s = np.ascontiguousarray(np.asarray(sites, dtype=np.int32))
         check(load_library().mps_apply_layer_device(self._h, k, len(s), _ip(s), ctypes.c_void_p(ptr)))
+
+    def layer_features(self, sites, Us) -> np.ndarray:
+        Us = _c128(Us)
+        s = np.ascontiguousarray(np.asarray(sites, dtype=np.int32))
+        X = np.zeros((len(s), 16), dtype=np.float32)
+        check(load_library().mps_layer_features(self._h, 2, len(s), _ip(s), _dp(Us.view(np.float64)),
+                                                X.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return X
+
+    def set_predictor(self, predictor) -> None:
+        check(load_library().mps_set_predictor(self._h, predictor._h if predictor is not None else None))
+        self._predictor = predictor  # keep it alive
+
+    def sketch_stats(self):
+        a, b, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        check(load_library().mps_sketch_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"sketched": a.value, "accepted": b.value, "routed_full": c.value}
 
     def profile(self, enable: bool) -> None:
         check(load_library().mps_profile(self._h, 1 if enable else 0))
@@ -308,3 +342,75 @@ def split_zgemm(A, B, slices: int = 8, stream=None):
                                          K, ctypes.c_void_p(Ct.data_ptr()), M, slices,
                                          ctypes.c_void_p(s) if s else None))
     return Ct.t()
+
+
+def apply_layer_multi(states, layers_per_state) -> int:
+    """One batched pass over the multi-qubit gates of several MPS.
+
+    states: list of MPS (the first one's stream, workspace and mode are used);
+    layers_per_state: for each MPS a list of (site, U) with U of one size k
+    (2 or 3 qubits), disjoint within each MPS. Returns the number of gates."""
+    ks = {U.shape[0] for layer in layers_per_state for (_, U) in layer}
+    if not ks:
+        return 0
+    assert len(ks) == 1, "one gate size per call"
+    k = {4: 2, 8: 3}[ks.pop()]
+    hs = (ctypes.c_void_p * len(states))(*[m._h.value for m in states])
+    n = np.ascontiguousarray([len(layer) for layer in layers_per_state], dtype=np.int32)
+    sites = np.ascontiguousarray([s for layer in layers_per_state for (s, _) in layer], dtype=np.int32)
+    Us = _c128(np.stack([U for layer in layers_per_state for (_, U) in layer]))
+    check(load_library().mps_apply_layer_multi(len(states), hs, k, _ip(n), _ip(sites), _dp(Us.view(np.float64))))
+    return int(n.sum())
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class RankPredictor:
+    """The 16-64-1 tanh MLP (fp32) trained and run by the library's kernels."""
+
+    def __init__(self, seed: int = 0):
+        h = ctypes.c_void_p()
+        check(load_library().mps_mlp_create(seed, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load_library().mps_mlp_destroy(h)
+        self._h = None
+
+    __del__ = close
+
+    @property
+    def params(self) -> np.ndarray:
+        p = np.zeros(MLP_PARAMS, dtype=np.float32)
+        check(load_library().mps_mlp_params(self._h, _fp(p), None))
+        return p
+
+    @params.setter
+    def params(self, p) -> None:
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        check(load_library().mps_mlp_params(self._h, None, _fp(p)))
+
+    def forward(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float32).reshape(-1, 16))
+        Y = np.zeros(X.shape[0], dtype=np.float32)
+        check(load_library().mps_mlp_forward(self._h, X.shape[0], _fp(X), _fp(Y)))
+        return Y
+
+    def loss_grad(self, X, T):
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float32).reshape(-1, 16))
+        T = np.ascontiguousarray(np.asarray(T, dtype=np.float32))
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.zeros(MLP_PARAMS, dtype=np.float32)
+        check(load_library().mps_mlp_loss_grad(self._h, X.shape[0], _fp(X), _fp(T), _fp(loss), _fp(g)))
+        return float(loss[0]), g
+
+    def train(self, X, T, epochs: int = 20, batch: int = 256, lr: float = 1e-3, seed: int = 0) -> float:
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float32).reshape(-1, 16))
+        T = np.ascontiguousarray(np.asarray(T, dtype=np.float32))
+        loss = np.zeros(1, dtype=np.float32)
+        check(load_library().mps_mlp_train(self._h, X.shape[0], _fp(X), _fp(T), epochs, batch, lr, seed, _fp(loss)))
+        return float(loss[0])

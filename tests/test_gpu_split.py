@@ -64,11 +64,9 @@ def test_split_gemm_error_falls_with_slices(torch):
     assert errs[1] < 2e-5 and errs[3] < 2e-9
 
 
-def test_split_gemm_rejects_long_k(torch):
-    from paper_1111_3124_gb300.mps import MPSError, split_zgemm
-    with pytest.raises(MPSError):
-        split_zgemm(torch.zeros((4, 513), dtype=torch.complex128, device="cuda"),
-                    torch.zeros((513, 4), dtype=torch.complex128, device="cuda"))
+@pytest.mark.parametrize("k", [513, 1024, 1500])
+def test_split_gemm_long_k_in_chunks(torch, k):
+    assert _gemm_err(torch, 130, 70, k, seed=k) < 8e-15
 
 
 # ------------------------------------------------------------- split updates ---
