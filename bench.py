@@ -8,7 +8,12 @@ Prints one JSON line (rank 0). See the design notes for the roofline
 definitions.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--prec fp64|split]
+                  [--prec split|fp64] [--no-fp64-compare]
+
+The headline is the split-precision path (bf16-sliced tensor-core products,
+fp32 preconditioning sweeps, binary64 angles, tests and polish); the native
+binary64 path is timed beside it on the same workload (`fp64_path`), with the
+split result's deviation from it.
 """
 from __future__ import annotations
 
@@ -55,7 +60,9 @@ def args_parse():
     p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--prec", default="fp64", choices=["fp64", "split"])
+    p.add_argument("--prec", default="split", choices=["fp64", "split"])
+    p.add_argument("--no-fp64-compare", action="store_true",
+                   help="skip timing the native binary64 path beside the split path")
     p.add_argument("--cpu-sample", type=int, default=2, help="oracle updates timed for cpu_baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--n", type=int, default=None, help="override the qubit count (small profiling cases)")
@@ -271,6 +278,40 @@ def run_gpu(a):
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
 
+    # ---- the native binary64 path on the same workload (one warm-up, one
+    # timed step) and the split result's deviation from it
+    fp64 = None
+    if a.prec == "split" and not a.no_fp64_compare:
+        with torch.cuda.stream(stream):
+            m2 = MPS(c["n"], c["chi_max"], c["cutoff"], PREC_FP64)
+            m2.set_stream(stream)
+
+            def step64():
+                m2.reset()
+                for k, s, dU in dev_layers:
+                    m2.apply_layer_device(s, dU, k)
+
+            step64()
+            m2.sync()
+            flush.fill_(-1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            step64()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t64 = e0.elapsed_time(e1) / 1e3
+            bits = np.random.default_rng(11).integers(0, 2, size=(256, c["n"])).astype(np.uint8)
+            a_sp, a_64 = m.amplitudes(bits), m2.amplitudes(bits)
+            spec = max(float(np.max(np.abs(m.schmidt(b) - m2.schmidt(b)))) / float(np.max(m2.schmidt(b)))
+                       if len(m.schmidt(b)) == len(m2.schmidt(b)) else float("inf") for b in range(c["n"] - 1))
+            fp64 = {"value": nup / t64, "unit": "updates/s", "ms_per_step": 1e3 * t64, "steps": 1, "warmup": 1,
+                    "split_speedup": None,
+                    "split_vs_fp64": {"max_abs_amp_err": float(np.max(np.abs(a_sp - a_64))),
+                                      "max_rel_amp_err": float(np.max(np.abs(a_sp - a_64)) / np.max(np.abs(a_64))),
+                                      "max_spectrum_err": spec, "amplitudes_sampled": int(len(bits))}}
+            m2.close()
+
     t_step = sum(times) / len(times) / 1e3
     t_e2e = e2e_s / a.steps
     if world > 1:
@@ -313,6 +354,9 @@ def run_gpu(a):
             "roofline": roof, "kernels": kernels, "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(prof[0]["launches_all"])}
+    if fp64 is not None:
+        fp64["split_speedup"] = value / world / fp64["value"]
+        line["fp64_path"] = fp64
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_obj(a.cpu_sample)
     if rank == 0:

@@ -244,8 +244,12 @@ int mps_import(mps_handle h, const int* chi, const double* gammas, const double*
  *   discarded[i]  discarded weight sum_{dropped} sigma^2 / sum sigma^2
  *                 (k = 3: sum over both splits)
  *   sweeps[i]     Jacobi sweeps used (k = 3: both splits)
+ *   k_sketch[i]   singular values above max(cutoff / 100, Mw eps) ||sigma||
+ *                 (before the chi_max cap): the rank a randomized sketch of
+ *                 this update must capture to be accepted (MPS_SVD_SKETCH_MLP);
+ *                 the rank predictor is trained on it
  * Any output pointer may be NULL. Synchronises the stream. */
-int mps_diag(mps_handle h, int cap, int* count, int* k, double* discarded, int* sweeps);
+int mps_diag(mps_handle h, int cap, int* count, int* k, double* discarded, int* sweeps, int* k_sketch);
 
 /* Per-kernel-class timing of later calls (not part of the method; used to
  * measure each kernel against its roofline). enable = 1 brackets every launch

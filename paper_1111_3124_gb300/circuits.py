@@ -66,6 +66,33 @@ def brickwork(n: int, depth: int, rng, first_u2_layer: bool = False, rz_after_ea
     return layers
 
 
+def weak_gate(rng: np.random.Generator, t_max: float = 0.3) -> np.ndarray:
+    """A weakly entangling U(4): exp(-i t (XX + YY + ZZ)), t ~ U[0, t_max),
+    dressed with Haar-random single-qubit gates on both sides."""
+    h = np.kron(X, X) + np.kron(Y, Y) + np.kron(Z, Z)
+    w, v = np.linalg.eigh(h)
+    t = rng.uniform(0.0, t_max)
+    core = (v * np.exp(-1j * t * w)[None, :]) @ v.conj().T
+    a = np.kron(haar_unitary(2, rng), haar_unitary(2, rng))
+    b = np.kron(haar_unitary(2, rng), haar_unitary(2, rng))
+    return np.ascontiguousarray(a @ core @ b)
+
+
+def weak_brickwork(n: int, depth: int, rng, t_max: float = 0.3):
+    """Brickwork of weakly entangling gates (Trotter-step-like circuits)."""
+    return [[(s, weak_gate(rng, t_max)) for s in brickwork_sites(n, l)] for l in range(depth)]
+
+
+def echo_brickwork(n: int, depth: int, rng, t_max: float = 0.3):
+    """Loschmidt echo: a weakly entangling brickwork followed by its exact
+    inverse (the layers reversed, each gate replaced by U^dagger). In the
+    second half each update lowers the entanglement of its bond, so the kept
+    rank falls well below theta's dimensions."""
+    fwd = weak_brickwork(n, depth, rng, t_max)
+    back = [[(s, np.ascontiguousarray(U.conj().T)) for s, U in layer] for layer in reversed(fwd)]
+    return fwd + back
+
+
 def ghz_prefix(n: int):
     layers = [[(0, H.copy())]]
     for q in range(n - 1):

@@ -3,10 +3,11 @@
 // A handle owns the Vidal-form tensors of one MPS in device memory (layout
 // in engine.cuh), a per-gate workspace that grows with the widest layer seen,
 // pinned staging buffers for gates and task tables, and a CUDA stream.
-// Bond dimensions live on the device; the host keeps only upper bounds
-// (ub[b+1] >= chi of bond b, exact for generic gates) to size grids, so a
-// layer's launches need no device-to-host read except the one-int
-// convergence count after each Jacobi sweep.
+// Bond dimensions live on the device; the host keeps upper bounds
+// (ub[b+1] >= chi of bond b) to size grids. Within a pass the only
+// device-to-host reads are the one-int convergence count after each Jacobi
+// sweep and the task metadata after the truncation, which makes the bounds
+// of the rewritten bonds exact.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,6 +24,7 @@
 #include "kernels.cuh"
 #include "mlp.cuh"
 #include "ozaki.cuh"
+#include "sketch.cuh"
 
 using namespace mpsgb;
 typedef std::complex<double> cd;
@@ -44,7 +46,7 @@ int fail(int code, const std::string& msg) {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                        \
   } while (0)
 
-constexpr int kMaxSweeps = 40;
+constexpr int kMaxSweeps = 60;
 
 constexpr int kProfKinds = 6;  // see mps_profile in include/mps.h
 constexpr int kSplitMaxCap = kMaxCap;  // the split GEMM chunks K beyond 512
@@ -98,6 +100,9 @@ struct mps_state {
   // learned rank predictor / sketch SVD
   mps_mlp* predictor = nullptr;
   long long sk_sketched = 0, sk_accepted = 0, sk_routed = 0;
+  unsigned long long sk_seed = 0x243F6A8885A308D3ull;
+  void* sk_arena = nullptr;  // sketch buffers, laid out per pass
+  size_t sk_bytes = 0;
   // split precision
   OzJob* d_oz_jobs = nullptr;
   int oz_cap = 0;
@@ -249,6 +254,7 @@ void free_state(mps_state* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   cudaFree(h->arena);
+  cudaFree(h->sk_arena);
   cudaFree(h->d_oz_jobs); cudaFree(h->d_oz_err); cudaFree(h->oz_buf.base);
   cudaFree(h->gamma); cudaFree(h->lambda); cudaFree(h->chi);
   cudaFree(h->d_tasks); cudaFree(h->d_meta); cudaFree(h->d_gates); cudaFree(h->d_counter);
@@ -333,9 +339,17 @@ int flush_pending(mps_state* h) {
 // Blocked one-sided Jacobi on every task's working matrix (A, or T for the
 // second split of a three-site update). One launch per round-robin round;
 // a sweep ends with a convergence count read back to the host.
+int run_svd_on(mps_state* h, const GateTask* dt, TaskMeta* dm, int ntask, int nw_ub, int second, bool init_v);
+
 int run_svd(mps_state* h, int ntask, int nw_ub, int second, bool init_v = true) {
+  return run_svd_on(h, h->d_tasks, h->d_meta, ntask, nw_ub, second, init_v);
+}
+
+// Jacobi sweeps on an explicit task/meta array (the layer's tasks, or the
+// sketch's small sub-problems).
+int run_svd_on(mps_state* h, const GateTask* dt, TaskMeta* dm, int ntask, int nw_ub, int second, bool init_v) {
   if (init_v) {
-    launch_init_V(h->d_tasks, h->d_meta, ntask, nw_ub, h->stream);
+    launch_init_V(dt, dm, ntask, nw_ub, h->stream);
     h->launches_all += 1;
   }
   const int nb = (nw_ub + kBlockW - 1) / kBlockW;
@@ -344,11 +358,11 @@ int run_svd(mps_state* h, int ntask, int nw_ub, int second, bool init_v = true) 
   for (int sw = 0; sw < kMaxSweeps; ++sw) {
     for (int r = 0; r < nbe - 1; ++r) {
       const int ev = pbeg(h);
-      launch_jacobi_round(h->d_tasks, h->d_meta, ntask, r, nbe / 2, second, fl, h->stream);
+      launch_jacobi_round(dt, dm, ntask, r, nbe / 2, second, fl, h->stream);
       pend(h, 0, ev, 1);
     }
     CK(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
-    launch_sweep_end(h->d_meta, ntask, kMaxSweeps, h->d_counter, h->stream);
+    launch_sweep_end(dm, ntask, kMaxSweeps, h->d_counter, h->stream);
     h->launches_all += 1;
     CK(cudaMemcpyAsync(h->h_counter, h->d_counter, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -372,7 +386,25 @@ int validate_layer(mps_state* h, int k, int ng, const int* sites, const void* Us
   return MPS_OK;
 }
 
+int ensure_oz(mps_state* h, int njobs) {
+  if (!h->d_oz_jobs || h->oz_cap < njobs) {
+    CK(cudaStreamSynchronize(h->stream));
+    cudaFree(h->d_oz_jobs);
+    h->d_oz_jobs = nullptr;
+    const int cap = std::max(njobs, h->task_cap);
+    CK(cudaMalloc(&h->d_oz_jobs, sizeof(OzJob) * cap));
+    h->oz_cap = cap;
+  }
+  if (!h->d_oz_err) {
+    CK(cudaMalloc(&h->d_oz_err, sizeof(int)));
+    CK(cudaMemset(h->d_oz_err, 0, sizeof(int)));
+  }
+  return MPS_OK;
+}
+
 int oz_gemm(mps_state* h, int ng, int kind, int M_ub, int N_ub, int K_ub) {
+  int rc0 = ensure_oz(h, ng);
+  if (rc0) return rc0;
   launch_oz_jobs(h->d_tasks, h->d_meta, h->d_oz_jobs, ng, kind, h->stream);
   const int ev = pbeg(h);
   const int rc = ozaki_zgemm(h->d_oz_jobs, ng, M_ub, N_ub, K_ub, h->slices, h->oz_buf, h->d_oz_err, h->stream);
@@ -387,7 +419,7 @@ int oz_gemm(mps_state* h, int ng, int kind, int M_ub, int N_ub, int K_ub) {
 // fp32 preconditioning sweeps on (A32, V32) of every task, then re-arm the
 // tasks (the binary64 sweeps reuse the active/sweep counters).
 int run_f32_sweeps(mps_state* h, int ng, int nw_ub) {
-  const int nb = (nw_ub + kBlockW - 1) / kBlockW;
+  const int nb = (nw_ub + kBlockW32 - 1) / kBlockW32;
   const int nbe = nb + (nb & 1);
   unsigned long long* fl = h->prof ? h->d_prof_flops + 4 : nullptr;
   for (int sw = 0; sw < kF32Sweeps; ++sw) {
@@ -410,16 +442,6 @@ int run_f32_sweeps(mps_state* h, int ng, int nw_ub) {
 // theta by the split GEMM, fp32 preconditioning sweeps, Newton-Schulz
 // re-orthonormalisation of V and B = A V by the split GEMM, binary64 sweeps.
 int run_split_theta_svd(mps_state* h, int ng, int xl_ub, int x0_ub, int xr_ub, int nw_ub) {
-  if (!h->d_oz_jobs || h->oz_cap < h->task_cap) {
-    cudaFree(h->d_oz_jobs);
-    h->d_oz_jobs = nullptr;
-    CK(cudaMalloc(&h->d_oz_jobs, sizeof(OzJob) * h->task_cap));
-    h->oz_cap = h->task_cap;
-  }
-  if (!h->d_oz_err) {
-    CK(cudaMalloc(&h->d_oz_err, sizeof(int)));
-    CK(cudaMemset(h->d_oz_err, 0, sizeof(int)));
-  }
   const int mw_ub = std::max(2 * xl_ub, 2 * xr_ub);
   int rc = oz_gemm(h, ng, kOzTheta, 2 * xl_ub, 2 * xr_ub, x0_ub);
   if (rc) return rc;
@@ -478,6 +500,17 @@ int run_split_theta_svd(mps_state* h, int ng, int xl_ub, int x0_ub, int xr_ub, i
 // The update pipeline of one pass of k-site gates (k = 2, 3), possibly from
 // several MPS: refs[g] is gate g, its matrix on the device at d_U + g*u_stride.
 // `w` owns the workspace, the task tables and the stream.
+// Reads the pass's task metadata back (one small copy after the pass's last
+// launch) so that the host bounds of the rewritten bonds become the kept
+// ranks themselves: the next layer's grids then follow the actual bond
+// dimensions instead of the growth bound min(chi_max, 2 chi_l, 2 chi_r).
+int read_meta(mps_state* w, int ng, std::vector<TaskMeta>& hm) {
+  hm.resize(ng);
+  CK(cudaMemcpyAsync(hm.data(), w->d_meta, sizeof(TaskMeta) * ng, cudaMemcpyDeviceToHost, w->stream));
+  CK(cudaStreamSynchronize(w->stream));
+  return MPS_OK;
+}
+
 int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const double2* d_U, int u_stride,
                     bool split) {
   const int ng = (int)refs.size();
@@ -558,20 +591,28 @@ int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const
     launch_emit_left(w->d_tasks, w->d_meta, ng, xl_ub, k_ub, 0, w->stream);
     launch_emit_right(w->d_tasks, w->d_meta, ng, xr_ub, k_ub, 0, w->stream);
     pend(w, 2, ev, 4);
-    for (const TaskRef& r : refs) {
-      mps_state* h = r.st;
-      h->ub[r.site + 1] = std::min(h->cap, std::min(2 * h->ub[r.site], 2 * h->ub[r.site + 2]));
+    std::vector<TaskMeta> hm;
+    if ((rc = read_meta(w, ng, hm))) return rc;
+    for (int g = 0; g < ng; ++g) {
+      mps_state* h = refs[g].st;
+      const int bound = std::min(h->cap, std::min(2 * h->ub[refs[g].site], 2 * h->ub[refs[g].site + 2]));
+      h->ub[refs[g].site + 1] = hm[g].status == 0 ? std::max(1, std::min(bound, hm[g].knew)) : bound;
     }
   } else {
     launch_emit_left(w->d_tasks, w->d_meta, ng, xl_ub, k_ub, 0, w->stream);
     launch_form_second(w->d_tasks, w->d_meta, ng, k_ub, xr_ub, w->stream);
     launch_setup(w->d_tasks, w->d_meta, ng, 1, w->stream);
     pend(w, 2, ev, 5);
+    std::vector<TaskMeta> hm;
+    if ((rc = read_meta(w, ng, hm))) return rc;
+    std::vector<int> k1s(ng);
     int nw2_ub = 1;
-    for (const TaskRef& r : refs) {
+    for (int g = 0; g < ng; ++g) {
+      const TaskRef& r = refs[g];
       const mps_state* h = r.st;
-      const int k1 = std::min(h->cap, std::min(2 * h->ub[r.site], 4 * h->ub[r.site + 3]));
-      nw2_ub = std::max(nw2_ub, std::min(2 * k1, 2 * h->ub[r.site + 3]));
+      const int bound = std::min(h->cap, std::min(2 * h->ub[r.site], 4 * h->ub[r.site + 3]));
+      k1s[g] = hm[g].status == 0 ? std::max(1, std::min(bound, hm[g].k1)) : bound;
+      nw2_ub = std::max(nw2_ub, std::min(2 * k1s[g], 2 * h->ub[r.site + 3]));
     }
     launch_frob(w->d_tasks, w->d_meta, ng, (long long)(2 * k_ub) * (2 * xr_ub), 1, w->stream);
     w->launches_all += 1;
@@ -584,16 +625,355 @@ int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const
     launch_emit_left(w->d_tasks, w->d_meta, ng, k_ub, k2_ub, 1, w->stream);
     launch_emit_right(w->d_tasks, w->d_meta, ng, xr_ub, k2_ub, 1, w->stream);
     pend(w, 2, ev, 4);
-    for (const TaskRef& r : refs) {
-      mps_state* h = r.st;
-      const int k1 = std::min(h->cap, std::min(2 * h->ub[r.site], 4 * h->ub[r.site + 3]));
-      h->ub[r.site + 1] = k1;
-      h->ub[r.site + 2] = std::min(h->cap, std::min(2 * k1, 2 * h->ub[r.site + 3]));
+    if ((rc = read_meta(w, ng, hm))) return rc;
+    for (int g = 0; g < ng; ++g) {
+      mps_state* h = refs[g].st;
+      const int s0 = refs[g].site;
+      const int bound = std::min(h->cap, std::min(2 * k1s[g], 2 * h->ub[s0 + 3]));
+      h->ub[s0 + 1] = k1s[g];
+      h->ub[s0 + 2] = hm[g].status == 0 ? std::max(1, std::min(bound, hm[g].knew)) : bound;
     }
   }
   CK(cudaGetLastError());
   w->last_ntask = ng;
   w->last_k = k;
+  return MPS_OK;
+}
+
+// ------------------------------------------------------------- sketch path ---
+
+// Split-precision GEMMs whose jobs are built on the host (exact dimensions).
+int oz_gemm_host(mps_state* w, const std::vector<OzJob>& jobs, int M_ub, int N_ub, int K_ub) {
+  if (jobs.empty()) return MPS_OK;
+  const int n = (int)jobs.size();
+  int rc0 = ensure_oz(w, n);
+  if (rc0) return rc0;
+  CK(cudaStreamSynchronize(w->stream));  // the job table is rewritten below
+  CK(cudaMemcpy(w->d_oz_jobs, jobs.data(), sizeof(OzJob) * n, cudaMemcpyHostToDevice));
+  const int ev = pbeg(w);
+  const int rc = ozaki_zgemm(w->d_oz_jobs, n, M_ub, N_ub, K_ub, w->slices, w->oz_buf, w->d_oz_err, w->stream);
+  const int npair = w->slices * (w->slices + 1) / 2;
+  pend(w, 3, ev, 3, (double)n * npair * 8.0 * M_ub * N_ub * K_ub);
+  if (rc == -2) return fail(MPS_ERR_NOMEM, "split GEMM buffers");
+  if (rc) return fail(MPS_ERR_CUDA, "split GEMM launch failed");
+  return MPS_OK;
+}
+
+OzView view(const double2* p, long long s_r, long long s_k, int conj = 0, const double* rscale = nullptr) {
+  OzView v = {};
+  v.p = p;
+  v.s_r = s_r;
+  v.s_k = s_k;
+  v.conj = conj;
+  v.rscale = rscale;
+  return v;
+}
+
+OzJob job(OzView a, OzView b, int M, int N, int K, double2* C, long long ldc) {
+  OzJob j = {};
+  j.a = a;
+  j.b = b;
+  j.M = M;
+  j.N = N;
+  j.K = K;
+  j.C = C;
+  j.ldc = ldc;
+  j.alpha = 1.0;
+  return j;
+}
+
+// Predicted kept rank of each two-site gate (features of the current state,
+// the MLP forward kernel on the device).
+int predict_ranks(mps_state* w, const std::vector<TaskRef>& refs, const double2* hU, std::vector<double>& rhat) {
+  const int n = (int)refs.size();
+  std::vector<FeatureTask> ft(n);
+  for (int g = 0; g < n; ++g) {
+    const TaskRef& r = refs[g];
+    double u[32];
+    for (int e = 0; e < 16; ++e) {
+      u[2 * e] = hU[64 * g + e].x;
+      u[2 * e + 1] = hU[64 * g + e].y;
+    }
+    FeatureTask f;
+    f.lamL = bond_ptr(r.st, r.site - 1);
+    f.lamR = bond_ptr(r.st, r.site + 1);
+    f.chi = r.st->chi;
+    f.site = r.site;
+    f.k = 2;
+    f.ep = (float)entangling_power(u);
+    f.cutoff = r.st->cutoff;
+    ft[g] = f;
+  }
+  FeatureTask* d_ft = nullptr;
+  float *d_x = nullptr, *d_y = nullptr;
+  CK(cudaMalloc(&d_ft, sizeof(FeatureTask) * n));
+  CK(cudaMalloc(&d_x, sizeof(float) * 16 * n));
+  CK(cudaMalloc(&d_y, sizeof(float) * n));
+  std::vector<float> y(n);
+  cudaError_t e = cudaMemcpyAsync(d_ft, ft.data(), sizeof(FeatureTask) * n, cudaMemcpyHostToDevice, w->stream);
+  if (e == cudaSuccess) {
+    launch_features(d_ft, n, d_x, w->stream);
+    launch_mlp_fwd(mlp_params(w->predictor), d_x, n, d_y, w->stream);
+    w->launches_all += 2;
+    e = cudaMemcpyAsync(y.data(), d_y, sizeof(float) * n, cudaMemcpyDeviceToHost, w->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
+  cudaFree(d_ft);
+  cudaFree(d_x);
+  cudaFree(d_y);
+  if (e != cudaSuccess) return fail(MPS_ERR_CUDA, "rank prediction");
+  rhat.resize(n);
+  for (int g = 0; g < n; ++g) rhat[g] = std::exp2(10.0 * std::min(std::max((double)y[g], -1.0), 1.1));
+  return MPS_OK;
+}
+
+__global__ void k_mark_skip(TaskMeta* meta, const int* idx, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) meta[idx[t]].status = 1;  // left to the full pass: no truncation or rewrite here
+}
+
+// One sketch pass over two-site gates S with sketch widths r (host gates hU,
+// folded, stride 64). Accepted gates are finished (truncated, rewritten);
+// the indices of rejected gates are returned for the full Jacobi pass.
+int run_sketch_pass(mps_state* w, const std::vector<TaskRef>& S, const std::vector<int>& rS, const double2* hU,
+                    std::vector<int>& rejected) {
+  const int ng = (int)S.size();
+  const bool split = w->prec == MPS_PREC_SPLIT;
+  CK(cudaStreamSynchronize(w->stream));
+  int rc = ensure_tasks(w, ng);
+  if (rc) return rc;
+  std::memcpy(w->h_gates, hU, sizeof(double2) * 64 * ng);
+  CK(cudaMemcpyAsync(w->d_gates, w->h_gates, sizeof(double2) * 64 * ng, cudaMemcpyHostToDevice, w->stream));
+  // main task layout (A, V, T, sigma, perm) and sketch buffers
+  std::vector<TaskLayout> lay(ng);
+  size_t total = 0, sk_total = 0;
+  int xl_ub = 1, x0_ub = 1, xr_ub = 1, nw_ub = 1, mw_ub = 1, r_ub = 1, cap_ub = 1;
+  std::vector<size_t> sk_off(ng);
+  for (int g = 0; g < ng; ++g) {
+    lay[g] = task_layout(S[g], 2, true);
+    total += lay[g].total;
+    const mps_state* h = S[g].st;
+    const int xl = h->ub[S[g].site], x0 = h->ub[S[g].site + 1], xr = h->ub[S[g].site + 2];
+    const size_t mw = std::max(2 * xl, 2 * xr), nw = std::min(2 * xl, 2 * xr), r = rS[g];
+    xl_ub = std::max(xl_ub, xl);
+    x0_ub = std::max(x0_ub, x0);
+    xr_ub = std::max(xr_ub, xr);
+    nw_ub = std::max(nw_ub, (int)nw);
+    mw_ub = std::max(mw_ub, (int)mw);
+    r_ub = std::max(r_ub, rS[g]);
+    cap_ub = std::max(cap_ub, h->cap);
+    sk_off[g] = sk_total;
+    sk_total += align256(sizeof(double2) * (3 * nw * r + mw * r + mw * nw + 2 * r * r));
+  }
+  rc = ensure_arena(w, total);
+  if (rc) return rc;
+  const size_t sig_bytes = align256(sizeof(double) * (size_t)r_ub * ng);
+  const size_t tab_bytes = align256(sizeof(SketchTask) * ng) + 2 * align256(sizeof(GateTask) * ng) +
+                           2 * align256(sizeof(TaskMeta) * ng) + align256(sizeof(double) * ng) +
+                           align256(sizeof(int) * ng) * 2;
+  if (sk_total + 2 * sig_bytes + tab_bytes > w->sk_bytes) {
+    cudaFree(w->sk_arena);
+    w->sk_arena = nullptr;
+    w->sk_bytes = 0;
+    const size_t want = sk_total + 2 * sig_bytes + tab_bytes;
+    CK(cudaMalloc(&w->sk_arena, want));
+    w->sk_bytes = want;
+  }
+  unsigned char* skb = static_cast<unsigned char*>(w->sk_arena);
+  unsigned char* p = skb + sk_total;
+  double* d_sigy = reinterpret_cast<double*>(p);
+  p += sig_bytes;
+  double* d_sigb = reinterpret_cast<double*>(p);
+  p += sig_bytes;
+  SketchTask* d_sk = reinterpret_cast<SketchTask*>(p);
+  p += align256(sizeof(SketchTask) * ng);
+  GateTask* d_suby = reinterpret_cast<GateTask*>(p);
+  p += align256(sizeof(GateTask) * ng);
+  GateTask* d_subb = reinterpret_cast<GateTask*>(p);
+  p += align256(sizeof(GateTask) * ng);
+  TaskMeta* d_mety = reinterpret_cast<TaskMeta*>(p);
+  p += align256(sizeof(TaskMeta) * ng);
+  TaskMeta* d_metb = reinterpret_cast<TaskMeta*>(p);
+  p += align256(sizeof(TaskMeta) * ng);
+  double* d_res = reinterpret_cast<double*>(p);
+  p += align256(sizeof(double) * ng);
+  int* d_acc = reinterpret_cast<int*>(p);
+  p += align256(sizeof(int) * ng);
+  int* d_idx = reinterpret_cast<int*>(p);
+
+  // gate tasks, setup, theta, ||A||_F
+  unsigned char* base = static_cast<unsigned char*>(w->arena);
+  for (int g = 0; g < ng; ++g) {
+    mps_state* h = S[g].st;
+    const int s0 = S[g].site;
+    unsigned char* tb = base;
+    base += lay[g].total;
+    GateTask t;
+    std::memset(&t, 0, sizeof(t));
+    t.g0 = site_ptr(h, s0);
+    t.g1 = site_ptr(h, s0 + 1);
+    t.lamL = bond_ptr(h, s0 - 1);
+    t.lam0 = bond_ptr(h, s0);
+    t.lam1 = bond_ptr(h, s0 + 1);
+    t.lamR = bond_ptr(h, s0 + 1);
+    t.chi = h->chi;
+    t.U = w->d_gates + 64 * g;
+    t.site = s0;
+    t.k = 2;
+    t.cap = h->cap;
+    t.cutoff = h->cutoff;
+    const size_t* o = lay[g].off;
+    t.A = reinterpret_cast<double2*>(tb + o[0]);
+    t.V = reinterpret_cast<double2*>(tb + o[1]);
+    t.T = reinterpret_cast<double2*>(tb + o[2]);
+    t.sigma = reinterpret_cast<double*>(tb + o[3]);
+    t.perm = reinterpret_cast<int*>(tb + o[4]);
+    w->h_tasks[g] = t;
+  }
+  CK(cudaMemcpyAsync(w->d_tasks, w->h_tasks, sizeof(GateTask) * ng, cudaMemcpyHostToDevice, w->stream));
+  launch_setup(w->d_tasks, w->d_meta, ng, 0, w->stream);
+  if (split) {
+    rc = oz_gemm(w, ng, kOzTheta, 2 * xl_ub, 2 * xr_ub, x0_ub);
+    if (rc) return rc;
+    launch_gate_mix2(w->d_tasks, w->d_meta, ng, xl_ub, xr_ub, w->stream);
+  } else {
+    const int ev = pbeg(w);
+    launch_contract2(w->d_tasks, w->d_meta, ng, xl_ub, xr_ub, w->stream);
+    pend(w, 1, ev, 1);
+  }
+  launch_frob(w->d_tasks, w->d_meta, ng, (long long)mw_ub * nw_ub, 0, w->stream);
+  w->launches_all += 3;
+  std::vector<TaskMeta> hm(ng);
+  CK(cudaMemcpyAsync(hm.data(), w->d_meta, sizeof(TaskMeta) * ng, cudaMemcpyDeviceToHost, w->stream));
+  CK(cudaStreamSynchronize(w->stream));
+
+  // sketch tasks with exact dimensions
+  std::vector<SketchTask> sk(ng);
+  for (int g = 0; g < ng; ++g) {
+    SketchTask& q = sk[g];
+    q.task = g;
+    q.id = (int)(w->sk_sketched + g);
+    q.Mw = hm[g].Mw;
+    q.Nw = hm[g].Nw;
+    q.r = std::min(rS[g], q.Nw);
+    q.rcap = r_ub;
+    q.cutoff = S[g].st->cutoff;
+    q.A = w->h_tasks[g].A;
+    q.V = w->h_tasks[g].V;
+    double2* b = reinterpret_cast<double2*>(skb + sk_off[g]);
+    const size_t nw = q.Nw, mw = q.Mw, r = q.r;
+    q.Om = b;
+    q.Y = q.Om + nw * r;
+    q.Z = q.Y + mw * r;
+    q.Bh = q.Z + nw * r;
+    q.T2 = q.Bh + nw * r;
+    q.Wy = q.T2 + mw * nw;
+    q.Wb = q.Wy + r * r;
+  }
+  CK(cudaMemcpyAsync(d_sk, sk.data(), sizeof(SketchTask) * ng, cudaMemcpyHostToDevice, w->stream));
+  CK(cudaMemsetAsync(d_res, 0, sizeof(double) * ng, w->stream));
+  launch_omega(d_sk, ng, (long long)nw_ub * r_ub, w->sk_seed, w->stream);
+  w->launches_all += 1;
+  // Y = A Omega. No power iteration: A (A^H A)^q Omega compresses the spectrum
+  // to sigma^(2q+1), which pushes directions far above the cutoff below the
+  // resolution of Y's orthonormalisation; the residual test guards acceptance.
+  std::vector<OzJob> J1;
+  for (const SketchTask& q : sk)
+    J1.push_back(job(view(q.A, 1, q.Mw), view(q.Om, q.Nw, 1), q.Mw, q.r, q.Nw, q.Y, q.Mw));
+  if ((rc = oz_gemm_host(w, J1, mw_ub, r_ub, nw_ub))) return rc;
+  // Q = orth(Y): one-sided Jacobi on Y, columns divided by their norms
+  auto sub_problem = [&](GateTask* d_sub, TaskMeta* d_met, double* d_sig, bool of_y, const std::vector<int>& which,
+                         int rows_ub) -> int {
+    const int ns = (int)which.size();
+    std::vector<GateTask> st(ns);
+    std::vector<TaskMeta> sm(ns);
+    for (int i = 0; i < ns; ++i) {
+      const SketchTask& q = sk[which[i]];
+      GateTask t;
+      std::memset(&t, 0, sizeof(t));
+      t.A = of_y ? q.Y : q.Bh;
+      t.V = of_y ? q.Wy : q.Wb;
+      t.sigma = d_sig + (size_t)which[i] * r_ub;
+      st[i] = t;
+      TaskMeta m;
+      std::memset(&m, 0, sizeof(m));
+      m.Mw = of_y ? q.Mw : q.Nw;
+      m.Nw = q.r;
+      m.M = m.Mw;
+      m.N = m.Nw;
+      m.tall = 1;
+      m.active = 1;
+      sm[i] = m;
+    }
+    CK(cudaMemcpyAsync(d_sub, st.data(), sizeof(GateTask) * ns, cudaMemcpyHostToDevice, w->stream));
+    CK(cudaMemcpyAsync(d_met, sm.data(), sizeof(TaskMeta) * ns, cudaMemcpyHostToDevice, w->stream));
+    launch_frob(d_sub, d_met, ns, (long long)rows_ub * r_ub, 0, w->stream);
+    int rc2 = run_svd_on(w, d_sub, d_met, ns, r_ub, 0, true);
+    if (rc2) return rc2;
+    launch_colnorms(d_sub, d_met, ns, r_ub, 0, w->stream);
+    w->launches_all += 2;
+    CK(cudaStreamSynchronize(w->stream));  // the host vectors above are released on return
+    return MPS_OK;
+  };
+  std::vector<int> all(ng);
+  for (int g = 0; g < ng; ++g) all[g] = g;
+  rc = sub_problem(d_suby, d_mety, d_sigy, true, all, mw_ub);
+  if (rc) return rc;
+  launch_scale_q(d_sk, ng, (long long)mw_ub * r_ub, d_sigy, d_mety, w->stream);
+  // B^H = A^H Q; T2 = Q B; residual ||A - T2||_F^2
+  std::vector<OzJob> J4, J5;
+  for (const SketchTask& q : sk) {
+    J4.push_back(job(view(q.A, q.Mw, 1, 1), view(q.Y, q.Mw, 1), q.Nw, q.r, q.Mw, q.Bh, q.Nw));
+    J5.push_back(job(view(q.Y, 1, q.Mw), view(q.Bh, 1, q.Nw, 1), q.Mw, q.Nw, q.r, q.T2, q.Mw));
+  }
+  if ((rc = oz_gemm_host(w, J4, nw_ub, r_ub, mw_ub)) || (rc = oz_gemm_host(w, J5, mw_ub, nw_ub, r_ub))) return rc;
+  launch_residual(d_sk, ng, (long long)mw_ub * nw_ub, d_res, w->stream);
+  launch_sketch_mark(d_sk, ng, d_res, d_acc, w->d_meta, w->stream);
+  w->launches_all += 3;
+  std::vector<int> acc(ng);
+  CK(cudaMemcpyAsync(acc.data(), d_acc, sizeof(int) * ng, cudaMemcpyDeviceToHost, w->stream));
+  CK(cudaStreamSynchronize(w->stream));
+  std::vector<int> yes;
+  rejected.clear();
+  for (int g = 0; g < ng; ++g) (acc[g] ? yes : rejected).push_back(g);
+  w->sk_sketched += ng;
+  w->sk_accepted += (long long)yes.size();
+  if (!yes.empty()) {
+    // SVD of B: Jacobi on B^H; A[:, j < r] = Q Wb diag(sigma_b); V = B^H Wb / sigma_b
+    rc = sub_problem(d_subb, d_metb, d_sigb, false, yes, nw_ub);
+    if (rc) return rc;
+    std::vector<OzJob> J6;
+    for (int g : yes) {
+      const SketchTask& q = sk[g];
+      J6.push_back(job(view(q.Y, 1, q.Mw), view(q.Wb, q.r, 1, 0, d_sigb + (size_t)g * r_ub), q.Mw, q.r, q.r, q.A,
+                       q.Mw));
+    }
+    if ((rc = oz_gemm_host(w, J6, mw_ub, r_ub, r_ub))) return rc;
+    launch_sketch_finish(d_sk, ng, (long long)nw_ub * nw_ub + (long long)mw_ub * nw_ub, d_sigb, d_acc, w->stream);
+    w->launches_all += 1;
+  }
+  if (!rejected.empty()) {
+    CK(cudaMemcpyAsync(d_idx, rejected.data(), sizeof(int) * rejected.size(), cudaMemcpyHostToDevice, w->stream));
+    k_mark_skip<<<((int)rejected.size() + 127) / 128, 128, 0, w->stream>>>(w->d_meta, d_idx, (int)rejected.size());
+    w->launches_all += 1;
+  }
+  // truncation and rewrite of the accepted gates
+  const int k_ub = std::min(cap_ub, r_ub);
+  const int ev = pbeg(w);
+  launch_colnorms(w->d_tasks, w->d_meta, ng, nw_ub, 0, w->stream);
+  launch_truncate(w->d_tasks, w->d_meta, ng, 0, kMaxCap, w->stream);
+  launch_emit_left(w->d_tasks, w->d_meta, ng, xl_ub, k_ub, 0, w->stream);
+  launch_emit_right(w->d_tasks, w->d_meta, ng, xr_ub, k_ub, 0, w->stream);
+  pend(w, 2, ev, 4);
+  std::vector<TaskMeta> hm2;
+  if ((rc = read_meta(w, ng, hm2))) return rc;
+  for (int g : yes) {
+    mps_state* h = S[g].st;
+    const int s0 = S[g].site;
+    const int bound = std::min(sk[g].r, std::min(h->cap, std::min(2 * h->ub[s0], 2 * h->ub[s0 + 2])));
+    h->ub[s0 + 1] = hm2[g].status == 0 ? std::max(1, std::min(bound, hm2[g].knew)) : bound;
+  }
+  CK(cudaGetLastError());
   return MPS_OK;
 }
 
@@ -603,6 +983,43 @@ int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const
 // d_U with stride u_stride.
 int run_refs_chunked(mps_state* w, int k, std::vector<TaskRef>& refs, const double2* h_U, const double2* d_U,
                      int u_stride) {
+  if (k == 2 && w->svd_mode == MPS_SVD_SKETCH_MLP && w->predictor && h_U && !refs.empty()) {
+    // rank prediction; gates predicted near full rank go straight to the full SVD
+    std::vector<double> rhat;
+      int rc = predict_ranks(w, refs, h_U, rhat);
+    if (rc) return rc;
+      std::vector<TaskRef> S, F;
+    std::vector<int> rS;
+    std::vector<double2> hS, hF;
+    for (size_t g = 0; g < refs.size(); ++g) {
+      const mps_state* h = refs[g].st;
+      const int nw = std::min(2 * h->ub[refs[g].site], 2 * h->ub[refs[g].site + 2]);
+      // the sketch pays off only well below full rank; a rank at chi_max is a
+      // truncation by rank, whose kept values a sketch does not reproduce exactly
+      const int r = std::min(nw, (int)std::ceil(1.1 * rhat[g]) + 10);
+      const bool sketch = 4 * r < 3 * nw && r < h->cap && h->cap <= kSplitMaxCap;
+      (sketch ? S : F).push_back(refs[g]);
+      std::vector<double2>& dst = sketch ? hS : hF;
+      dst.insert(dst.end(), h_U + 64 * g, h_U + 64 * (g + 1));
+      if (sketch) rS.push_back(std::max(r, 1));
+    }
+    w->sk_routed += (long long)F.size();
+    if (!S.empty()) {
+      std::vector<int> rej;
+      rc = run_sketch_pass(w, S, rS, hS.data(), rej);
+      if (rc) return rc;
+      for (int g : rej) {
+        F.push_back(S[g]);
+        hF.insert(hF.end(), hS.begin() + 64 * g, hS.begin() + 64 * (g + 1));
+      }
+    }
+    if (F.empty()) return MPS_OK;
+    const int saved = w->svd_mode;
+    w->svd_mode = MPS_SVD_JACOBI;
+    rc = run_refs_chunked(w, k, F, hF.data(), nullptr, 0);
+    w->svd_mode = saved;
+      return rc;
+  }
   bool split = k == 2 && w->prec == MPS_PREC_SPLIT;
   for (const TaskRef& r : refs) split = split && r.st->cap <= kSplitMaxCap;
   size_t g0 = 0;
@@ -1176,7 +1593,7 @@ int mps_import(mps_handle h, const int* chi, const double* gammas, const double*
   return MPS_OK;
 }
 
-int mps_diag(mps_handle h, int cap, int* count, int* k, double* discarded, int* sweeps) {
+int mps_diag(mps_handle h, int cap, int* count, int* k, double* discarded, int* sweeps, int* k_sketch) {
   if (!h || !count || cap < 0) return fail(MPS_ERR_ARG, "bad arguments");
   CK(cudaStreamSynchronize(h->stream));
   *count = h->last_ntask;
@@ -1188,6 +1605,7 @@ int mps_diag(mps_handle h, int cap, int* count, int* k, double* discarded, int* 
       if (k) k[i] = t[i].knew;
       if (discarded) discarded[i] = t[i].disc;
       if (sweeps) sweeps[i] = t[i].sweeps_total;
+      if (k_sketch) k_sketch[i] = t[i].ksk;
     }
   }
   return MPS_OK;

@@ -60,6 +60,7 @@ struct TaskMeta {
   int status;           // 0 or an mps_status code
   int knew;             // kept rank of the current split
   int k1;               // kept rank of the first split (k = 3)
+  int ksk;              // singular values above max(cutoff/100, Mw eps) ||sigma||: the rank a sketch must capture
   double disc;          // discarded weight (summed over splits)
   double kept_norm;     // sqrt(sum of kept sigma^2) of the current split
   double frob2;         // ||A||_F^2 of the current working matrix

@@ -4,8 +4,11 @@
 
 namespace mpsgb {
 
-constexpr int kBlockW = 8;  // Jacobi block width b (columns per block)
+constexpr int kBlockW = 8;     // Jacobi block width b (columns per block), binary64 sweeps
+constexpr int kBlockW32 = 16;  // block width of the fp32 preconditioning sweeps
 constexpr float kQuadStop = 1e-8f;  // binary64 sweeps stop after one whose max scaled off-diagonal < this
+constexpr int kInnerSweepsFar = 1;  // inner sweeps of a block pair whose off-diagonal is above kQuadStop ...
+constexpr int kInnerFarSweeps = 30;  // ... during a task's first sweeps
 
 // Sets the message returned by mps_last_error() on the calling thread.
 void set_error_message(const char* msg);

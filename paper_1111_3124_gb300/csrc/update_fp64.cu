@@ -286,9 +286,9 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   typedef typename Cx<R>::T C;
   constexpr double EPS = Cx<R>::eps;
   constexpr int C2 = 2 * BW;
-  constexpr int NE = C2 * (C2 + 1) / 2;
-  constexpr int RCH = 64;
-  static_assert(NE <= 256 && C2 * C2 / 2 <= 256, "block too wide for one pass");
+  constexpr int NE = C2 * (C2 + 1) / 2;        // Gram entries (p <= q)
+  constexpr int EPT = (NE + 255) / 256;        // Gram entries per thread
+  constexpr int RCH = BW <= 8 ? 64 : 32;       // rows per staged chunk
   TaskMeta& mt = meta[blockIdx.y];
   if (!mt.active) return;
   const GateTask& tk = tasks[blockIdx.y];
@@ -329,17 +329,26 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
     need = 0;
     nrot = 0;
   }
-  // (p,q) of this thread's Gram entry, p <= q
-  int gp = 0, gq = 0;
-  if (tid < NE) {
-    int rem = tid;
-    while (rem >= C2 - gp) { rem -= C2 - gp; ++gp; }
-    gq = gp + rem;
+  // (p,q) of this thread's Gram entries tid, tid + 256, ...; p <= q
+  int gp[EPT], gq[EPT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int ent = tid + 256 * u;
+    gp[u] = 0;
+    gq[u] = 0;
+    if (ent < NE) {
+      int rem = ent, pp = 0;
+      while (rem >= C2 - pp) { rem -= C2 - pp; ++pp; }
+      gp[u] = pp;
+      gq[u] = pp + rem;
+    }
   }
   __syncthreads();
 
   // ---- Gram G = [A_I A_J]^H [A_I A_J]
-  C g = zero;
+  C gacc[EPT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) gacc[u] = zero;
   for (int r0 = 0; r0 < Mw; r0 += RCH) {
     for (int e = tid; e < RCH * C2; e += 256) {
       const int col = e / RCH, row = e % RCH;
@@ -347,16 +356,21 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
       chunk[row][col] = (gc >= 0 && r0 + row < Mw) ? A[(size_t)(r0 + row) + (size_t)gc * Mw] : zero;
     }
     __syncthreads();
-    if (tid < NE) {
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      if (tid + 256 * u < NE) {
 #pragma unroll 8
-      for (int row = 0; row < RCH; ++row) g = cfma_cj(chunk[row][gp], chunk[row][gq], g);
+        for (int row = 0; row < RCH; ++row) gacc[u] = cfma_cj(chunk[row][gp[u]], chunk[row][gq[u]], gacc[u]);
+      }
     }
     __syncthreads();
   }
-  if (tid < NE) {
-    G[gp][gq] = g;
-    G[gq][gp] = cconj(g);
-  }
+#pragma unroll
+  for (int u = 0; u < EPT; ++u)
+    if (tid + 256 * u < NE) {
+      G[gp[u]][gq[u]] = gacc[u];
+      G[gq[u]][gp[u]] = cconj(gacc[u]);
+    }
   __syncthreads();
   // ---- convergence test on the actual columns: |g_pq| <= Mw eps sqrt(g_pp g_qq),
   // numerically zero columns (g_jj <= (Mw eps)^2 ||A||_F^2) excluded
@@ -369,13 +383,16 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   __shared__ unsigned int smax;
   if (tid == 0) smax = 0u;
   __syncthreads();
-  if (tid < NE && gp != gq) {
-    const double app = (double)G[gp][gp].x, aqq = (double)G[gq][gq].x;
-    const double gabs = hypot((double)g.x, (double)g.y);
-    if (app > tiny && aqq > tiny) {
-      const double ratio = gabs / (sqrt(app) * sqrt(aqq));
-      if (ratio > tolc) need = 1;
-      atomicMax(&smax, __float_as_uint((float)ratio));
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    if (tid + 256 * u < NE && gp[u] != gq[u]) {
+      const double app = (double)G[gp[u]][gp[u]].x, aqq = (double)G[gq[u]][gq[u]].x;
+      const double gabs = hypot((double)gacc[u].x, (double)gacc[u].y);
+      if (app > tiny && aqq > tiny) {
+        const double ratio = gabs / (sqrt(app) * sqrt(aqq));
+        if (ratio > tolc) need = 1;
+        atomicMax(&smax, __float_as_uint((float)ratio));
+      }
     }
   }
   __syncthreads();
@@ -390,7 +407,13 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   // ---- Hermitian Jacobi on G (two-sided, cyclic by circle-method rounds)
   for (int e = tid; e < C2 * C2; e += 256) W[e / C2][e % C2] = mkc<C, R>((e / C2) == (e % C2) ? (R)1 : (R)0, (R)0);
   __syncthreads();
-  for (int isw = 0; isw < 24; ++isw) {
+  // Far from convergence, in the first sweeps, one inner sweep per pairing
+  // (block Jacobi with an approximate inner solve: every rotation still lowers
+  // off(A^H A), and the outer test above uses the fresh Gram); near
+  // convergence, or once a hard matrix has used those sweeps, the inner solve
+  // runs to convergence (the quadratic stop relies on it).
+  const int inner_max = __uint_as_float(smax) > kQuadStop && mt.sweeps < kInnerFarSweeps ? kInnerSweepsFar : 24;
+  for (int isw = 0; isw < inner_max; ++isw) {
     if (tid == 0) any = 0;
     __syncthreads();
     for (int ir = 0; ir < C2 - 1; ++ir) {
@@ -584,7 +607,8 @@ __global__ void __launch_bounds__(1024) k_truncate(const GateTask* tasks, TaskMe
   const double rel = fmax(tk.cutoff, (double)mt.Mw * kEps);  // values at the SVD's resolution count as zero
   const double thr = rel * sqrt(total);
   // rank_j = #{i: s_i > s_j} + #{i < j: s_i == s_j}
-  int cntp = 0;
+  const double thr_sk = fmax(0.01 * tk.cutoff, (double)mt.Mw * kEps) * sqrt(total);
+  int cntp = 0, cskp = 0;
   for (int j = threadIdx.x; j < nw; j += blockDim.x) {
     const double sj = sg[j];
     int rank = 0;
@@ -594,8 +618,10 @@ __global__ void __launch_bounds__(1024) k_truncate(const GateTask* tasks, TaskMe
     }
     tk.perm[rank] = j;
     cntp += sj > thr;
+    cskp += sj > thr_sk;
   }
   const int cnt = (int)block_sum((double)cntp, red);
+  const int csk = (int)block_sum((double)cskp, red);
   const int cap_k = chi_cap < tk.cap ? chi_cap : tk.cap;
   int k = cnt < cap_k ? cnt : cap_k;
   if (k < 1) k = 1;
@@ -614,6 +640,7 @@ __global__ void __launch_bounds__(1024) k_truncate(const GateTask* tasks, TaskMe
   if (threadIdx.x == 0) {
     tk.chi[tk.site + 1 + stage] = k;
     mt.knew = k;
+    mt.ksk = csk;
     if (stage == 0) mt.k1 = k;
     mt.disc += total > 0.0 ? dropped / total : 0.0;
     mt.kept_norm = nk;
@@ -785,7 +812,7 @@ void launch_sweep_end_nofail(TaskMeta* m, int ntask, int max_sweeps, int* active
 
 void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub,
                              unsigned long long* flops, cudaStream_t st) {
-  k_jacobi_pair<kBlockW, float><<<dim3(pairs_ub, ntask), 256, 0, st>>>(t, m, round, 0, flops);
+  k_jacobi_pair<kBlockW32, float><<<dim3(pairs_ub, ntask), 256, 0, st>>>(t, m, round, 0, flops);
 }
 
 void launch_colnorms(const GateTask* t, const TaskMeta* m, int ntask, int nw_ub, int second, cudaStream_t st) {

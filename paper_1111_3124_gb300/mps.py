@@ -80,7 +80,7 @@ def load_library(path: str = LIB_PATH):
         "mps_bond_dims": [P, ip],
         "mps_export": [P, ip, dp, dp],
         "mps_import": [P, ip, dp, dp],
-        "mps_diag": [P, I, ip, ip, dp, ip],
+        "mps_diag": [P, I, ip, ip, dp, ip, ip],
         "mps_sync": [P],
         "mps_gate2_update_noalloc": [P, P, P, P, P, P, I, D, dp, P],
         "mps_split_zgemm": [I, I, I, P, ctypes.c_longlong, P, ctypes.c_longlong, P, ctypes.c_longlong, I, P],
@@ -285,13 +285,14 @@ class MPS:
     def diag(self):
         cnt = ctypes.c_int()
         L = load_library()
-        check(L.mps_diag(self._h, 0, ctypes.byref(cnt), None, None, None))
+        check(L.mps_diag(self._h, 0, ctypes.byref(cnt), None, None, None, None))
         m = cnt.value
         k = np.zeros(max(m, 1), dtype=np.int32)
         w = np.zeros(max(m, 1))
         sw = np.zeros(max(m, 1), dtype=np.int32)
-        check(L.mps_diag(self._h, m, ctypes.byref(cnt), _ip(k), _dp(w), _ip(sw)))
-        return {"k": k[:m], "discarded": w[:m], "sweeps": sw[:m]}
+        ks = np.zeros(max(m, 1), dtype=np.int32)
+        check(L.mps_diag(self._h, m, ctypes.byref(cnt), _ip(k), _dp(w), _ip(sw), _ip(ks)))
+        return {"k": k[:m], "discarded": w[:m], "sweeps": sw[:m], "k_sketch": ks[:m]}
 
     def sync(self) -> None:
         check(load_library().mps_sync(self._h))
