@@ -287,8 +287,9 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   constexpr double EPS = Cx<R>::eps;
   constexpr int C2 = 2 * BW;
   constexpr int NE = C2 * (C2 + 1) / 2;        // Gram entries (p <= q)
-  constexpr int EPT = (NE + 255) / 256;        // Gram entries per thread
   constexpr int RCH = BW <= 8 ? 64 : 32;       // rows per staged chunk
+  constexpr int CPT = RCH * C2 / 256;          // rotated outputs per thread (one row, CPT columns)
+  static_assert(RCH * C2 == 256 * CPT, "rotation tiling");
   TaskMeta& mt = meta[blockIdx.y];
   if (!mt.active) return;
   const GateTask& tk = tasks[blockIdx.y];
@@ -329,48 +330,82 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
     need = 0;
     nrot = 0;
   }
-  // (p,q) of this thread's Gram entries tid, tid + 256, ...; p <= q
-  int gp[EPT], gq[EPT];
-#pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    const int ent = tid + 256 * u;
-    gp[u] = 0;
-    gq[u] = 0;
-    if (ent < NE) {
-      int rem = ent, pp = 0;
-      while (rem >= C2 - pp) { rem -= C2 - pp; ++pp; }
-      gp[u] = pp;
-      gq[u] = pp + rem;
-    }
-  }
   __syncthreads();
 
   // ---- Gram G = [A_I A_J]^H [A_I A_J]
-  C gacc[EPT];
-#pragma unroll
-  for (int u = 0; u < EPT; ++u) gacc[u] = zero;
-  for (int r0 = 0; r0 < Mw; r0 += RCH) {
-    for (int e = tid; e < RCH * C2; e += 256) {
-      const int col = e / RCH, row = e % RCH;
-      const int gc = cols[col];
-      chunk[row][col] = (gc >= 0 && r0 + row < Mw) ? A[(size_t)(r0 + row) + (size_t)gc * Mw] : zero;
+  if constexpr (sizeof(R) == 4) {
+    // fp32: 2 x 2 tiles of the upper block triangle, four independent
+    // accumulators per thread
+    constexpr int H = C2 / 2, NT = H * (H + 1) / 2;
+    static_assert(NT <= 256, "block too wide");
+    int ti = 0, tj = 0;
+    if (tid < NT) {
+      int rem = tid;
+      while (rem >= H - ti) { rem -= H - ti; ++ti; }
+      tj = ti + rem;
     }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < EPT; ++u) {
-      if (tid + 256 * u < NE) {
+    C a00 = zero, a01 = zero, a10 = zero, a11 = zero;
+    for (int r0 = 0; r0 < Mw; r0 += RCH) {
+      for (int e = tid; e < RCH * C2; e += 256) {
+        const int col = e / RCH, row = e % RCH;
+        const int gc = cols[col];
+        chunk[row][col] = (gc >= 0 && r0 + row < Mw) ? A[(size_t)(r0 + row) + (size_t)gc * Mw] : zero;
+      }
+      __syncthreads();
+      if (tid < NT) {
 #pragma unroll 8
-        for (int row = 0; row < RCH; ++row) gacc[u] = cfma_cj(chunk[row][gp[u]], chunk[row][gq[u]], gacc[u]);
+        for (int row = 0; row < RCH; ++row) {
+          const C x0 = chunk[row][2 * ti], x1 = chunk[row][2 * ti + 1];
+          const C y0 = chunk[row][2 * tj], y1 = chunk[row][2 * tj + 1];
+          a00 = cfma_cj(x0, y0, a00);
+          a01 = cfma_cj(x0, y1, a01);
+          a10 = cfma_cj(x1, y0, a10);
+          a11 = cfma_cj(x1, y1, a11);
+        }
+      }
+      __syncthreads();
+    }
+    if (tid < NT) {
+      const int p0 = 2 * ti, q0 = 2 * tj;
+      G[p0][q0] = a00;
+      G[p0][q0 + 1] = a01;
+      G[p0 + 1][q0] = a10;
+      G[p0 + 1][q0 + 1] = a11;
+      if (ti != tj) {
+        G[q0][p0] = cconj(a00);
+        G[q0 + 1][p0] = cconj(a01);
+        G[q0][p0 + 1] = cconj(a10);
+        G[q0 + 1][p0 + 1] = cconj(a11);
       }
     }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int u = 0; u < EPT; ++u)
-    if (tid + 256 * u < NE) {
-      G[gp[u]][gq[u]] = gacc[u];
-      G[gq[u]][gp[u]] = cconj(gacc[u]);
+  } else {
+    // binary64 (FP64-pipe bound): one upper-triangle entry per thread
+    static_assert(NE <= 256, "block too wide");
+    int gp = 0, gq = 0;
+    if (tid < NE) {
+      int rem = tid;
+      while (rem >= C2 - gp) { rem -= C2 - gp; ++gp; }
+      gq = gp + rem;
     }
+    C g = zero;
+    for (int r0 = 0; r0 < Mw; r0 += RCH) {
+      for (int e = tid; e < RCH * C2; e += 256) {
+        const int col = e / RCH, row = e % RCH;
+        const int gc = cols[col];
+        chunk[row][col] = (gc >= 0 && r0 + row < Mw) ? A[(size_t)(r0 + row) + (size_t)gc * Mw] : zero;
+      }
+      __syncthreads();
+      if (tid < NE) {
+#pragma unroll 8
+        for (int row = 0; row < RCH; ++row) g = cfma_cj(chunk[row][gp], chunk[row][gq], g);
+      }
+      __syncthreads();
+    }
+    if (tid < NE) {
+      G[gp][gq] = g;
+      G[gq][gp] = cconj(g);
+    }
+  }
   __syncthreads();
   // ---- convergence test on the actual columns: |g_pq| <= Mw eps sqrt(g_pp g_qq),
   // numerically zero columns (g_jj <= (Mw eps)^2 ||A||_F^2) excluded
@@ -383,15 +418,25 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   __shared__ unsigned int smax;
   if (tid == 0) smax = 0u;
   __syncthreads();
-#pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    if (tid + 256 * u < NE && gp[u] != gq[u]) {
-      const double app = (double)G[gp[u]][gp[u]].x, aqq = (double)G[gq[u]][gq[u]].x;
-      const double gabs = hypot((double)gacc[u].x, (double)gacc[u].y);
+  for (int e = tid; e < C2 * C2; e += 256) {
+    const int pp = e / C2, qq = e % C2;
+    if (pp >= qq) continue;
+    if constexpr (sizeof(R) == 8) {
+      const double app = G[pp][pp].x, aqq = G[qq][qq].x;
+      const double gabs = hypot(G[pp][qq].x, G[pp][qq].y);
       if (app > tiny && aqq > tiny) {
         const double ratio = gabs / (sqrt(app) * sqrt(aqq));
         if (ratio > tolc) need = 1;
         atomicMax(&smax, __float_as_uint((float)ratio));
+      }
+    } else {
+      // the fp32 preconditioner's own stopping test, at fp32 resolution (the
+      // binary64 sweeps that follow make the binary64 test)
+      const float app = G[pp][pp].x, aqq = G[qq][qq].x;
+      if ((double)app > tiny && (double)aqq > tiny) {
+        const float ratio = hypotf(G[pp][qq].x, G[pp][qq].y) * (rsqrtf(app) * rsqrtf(aqq));
+        if (ratio > (float)tolc) need = 1;
+        atomicMax(&smax, __float_as_uint(ratio));
       }
     }
   }
@@ -490,7 +535,10 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
     if (!any_r) break;
   }
 
-  // ---- rotate the columns of A (Mw rows) and of V (Nw rows) by W
+  // ---- rotate the columns of A (Mw rows) and of V (Nw rows) by W: each
+  // thread one row of the staged chunk and CPT consecutive output columns
+  // (independent accumulators; W's row k is a broadcast across the warp)
+  const int rrow = tid % RCH, c0 = (tid / RCH) * CPT;
   for (int pass = 0; pass < 2; ++pass) {
     C* Mx = pass == 0 ? A : Vm;
     const int rows = pass == 0 ? Mw : Nw;
@@ -501,14 +549,21 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
         chunk[row][col] = (gc >= 0 && r0 + row < rows) ? Mx[(size_t)(r0 + row) + (size_t)gc * rows] : zero;
       }
       __syncthreads();
-      for (int e = tid; e < RCH * C2; e += 256) {
-        const int col = e / RCH, row = e % RCH;
-        const int gc = cols[col];
-        if (gc < 0 || r0 + row >= rows) continue;
-        C o = zero;
+      if (r0 + rrow < rows) {
+        C o[CPT];
 #pragma unroll
-        for (int k = 0; k < C2; ++k) o = cfma(chunk[row][k], W[k][col], o);
-        Mx[(size_t)(r0 + row) + (size_t)gc * rows] = o;
+        for (int c = 0; c < CPT; ++c) o[c] = zero;
+#pragma unroll
+        for (int k = 0; k < C2; ++k) {
+          const C x = chunk[rrow][k];
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) o[c] = cfma(x, W[k][c0 + c], o[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          const int gc = cols[c0 + c];
+          if (gc >= 0) Mx[(size_t)(r0 + rrow) + (size_t)gc * rows] = o[c];
+        }
       }
       __syncthreads();
     }
