@@ -316,8 +316,9 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   __shared__ C chunk[RCH][C2 + 1];
   __shared__ C G[C2][C2 + 1];
   __shared__ C W[C2][C2 + 1];
-  __shared__ double rc_c[C2 / 2], rc_t[C2 / 2], rc_g[C2 / 2], rc_a[C2 / 2], rc_b[C2 / 2];
-  __shared__ double2 rc_se[C2 / 2];
+  __shared__ double rc_t[C2 / 2], rc_g[C2 / 2], rc_a[C2 / 2], rc_b[C2 / 2];
+  __shared__ R rc_c[C2 / 2];   // cos of the binary64 angle, rounded once to the working type
+  __shared__ C rc_se[C2 / 2];  // s e^{i phi}, likewise
   __shared__ int rc_on[C2 / 2];
   __shared__ int need, any, nrot;
   const int tid = threadIdx.x;
@@ -415,6 +416,7 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   // numerically zero columns: at binary64 resolution in both precisions, so the
   // fp32 passes still orthogonalise small (but nonzero) columns
   const double tiny = (double)Mw * kEps * (double)Mw * kEps * mt.frob2;
+  const float tinyf = (float)tiny;  // a value that rounds to it compares the same way up to one ulp
   __shared__ unsigned int smax;
   if (tid == 0) smax = 0u;
   __syncthreads();
@@ -433,7 +435,7 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
       // the fp32 preconditioner's own stopping test, at fp32 resolution (the
       // binary64 sweeps that follow make the binary64 test)
       const float app = G[pp][pp].x, aqq = G[qq][qq].x;
-      if ((double)app > tiny && (double)aqq > tiny) {
+      if (app > tinyf && aqq > tinyf) {
         const float ratio = hypotf(G[pp][qq].x, G[pp][qq].y) * (rsqrtf(app) * rsqrtf(aqq));
         if (ratio > (float)tolc) need = 1;
         atomicMax(&smax, __float_as_uint(ratio));
@@ -478,12 +480,12 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
           if (zeta < 0) t = -t;
           const double c = 1.0 / sqrt(1.0 + t * t);
           const double s = c * t;
-          rc_c[tid] = c;
+          rc_c[tid] = (R)c;
           rc_t[tid] = t;
           rc_g[tid] = gabs;
           rc_a[tid] = al;
           rc_b[tid] = be;
-          rc_se[tid] = make_double2(s * gx / gabs, s * gy / gabs);  // s e^{i phi}
+          rc_se[tid] = mkc<C, R>((R)(s * gx / gabs), (R)(s * gy / gabs));  // s e^{i phi}
           any = 1;
           atomicAdd(&nrot, 1);
         }
@@ -495,8 +497,8 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
         if (!rc_on[pr]) continue;
         int pp, qq;
         rr_pair(C2, ir, pr, pp, qq);
-        const R c = (R)rc_c[pr];
-        const C se = mkc<C, R>((R)rc_se[pr].x, (R)rc_se[pr].y);
+        const R c = rc_c[pr];
+        const C se = rc_se[pr];
         const C x = G[pp][col], y = G[qq][col];
         const C sy = cmul(se, y), cx = cmul(cconj(se), x);
         G[pp][col] = mkc<C, R>(c * x.x - sy.x, c * x.y - sy.y);
@@ -512,8 +514,8 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
         int pp, qq;
         rr_pair(C2, ir, pr, pp, qq);
         C(*Mx)[C2 + 1] = which ? W : G;
-        const R c = (R)rc_c[pr];
-        const C se = mkc<C, R>((R)rc_se[pr].x, (R)rc_se[pr].y);
+        const R c = rc_c[pr];
+        const C se = rc_se[pr];
         const C x = Mx[row][pp], y = Mx[row][qq];
         const C sy = cmul(cconj(se), y), sx = cmul(se, x);
         Mx[row][pp] = mkc<C, R>(c * x.x - sy.x, c * x.y - sy.y);
