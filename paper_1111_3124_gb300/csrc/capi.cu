@@ -51,6 +51,7 @@ constexpr int kMaxSweeps = 60;
 constexpr int kProfKinds = 6;  // see mps_profile in include/mps.h
 constexpr int kSplitMaxCap = kMaxCap;  // the split GEMM chunks K beyond 512
 constexpr int kF32Sweeps = 30;
+constexpr int kGramSteps = 2;  // simultaneous-rotation steps of the split path's Gram polish
 
 // Memory budget of one batched pass: the tasks of a layer (or of many
 // circuits' layers) are processed in chunks whose workspace fits this.
@@ -487,13 +488,43 @@ int run_split_theta_svd(mps_state* h, int ng, int xl_ub, int x0_ub, int xr_ub, i
       pend(h, 5, ev, 1);
     }
   }
+  // Gram polish: simultaneous first-order rotations from a split-precision
+  // Gram, then a last Gram test; what is left goes to the blocked sweeps
+  const long long nv = (long long)nw_ub * nw_ub, na = (long long)mw_ub * nw_ub;
+  for (int step = 0; step <= kGramSteps; ++step) {
+    const bool last = step == kGramSteps;
+    rc = oz_gemm(h, ng, kOzAhA, nw_ub, nw_ub, mw_ub);
+    if (rc) return rc;
+    ev = pbeg(h);
+    launch_gram_diag(h->d_tasks, h->d_meta, ng, nw_ub, h->stream);
+    launch_gram_x(h->d_tasks, h->d_meta, ng, nv, last ? 0 : 1, h->stream);
+    if (last) CK(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
+    launch_gram_end(h->d_meta, ng, last ? 1 : 0, h->d_counter, h->stream);
+    pend(h, 5, ev, 3);
+    if (last) break;
+    if ((rc = oz_gemm(h, ng, kOzXX, nw_ub, nw_ub, nw_ub))) return rc;  // Q = X^2
+    if ((rc = oz_gemm(h, ng, kOzX3, nw_ub, nw_ub, nw_ub))) return rc;  // V2 = X^3
+    if ((rc = oz_gemm(h, ng, kOzX4, nw_ub, nw_ub, nw_ub))) return rc;  // T = X^4
+    ev = pbeg(h);
+    launch_form_w(h->d_tasks, h->d_meta, ng, nv, h->stream);
+    launch_gram_scales(h->d_tasks, h->d_meta, ng, nw_ub, h->stream);
+    pend(h, 5, ev, 2);
+    if ((rc = oz_gemm(h, ng, kOzAW, mw_ub, nw_ub, nw_ub))) return rc;
+    if ((rc = oz_gemm(h, ng, kOzVW, nw_ub, nw_ub, nw_ub))) return rc;
+    ev = pbeg(h);
+    launch_take_t(h->d_tasks, h->d_meta, ng, na + nv, h->stream);
+    launch_givens(h->d_tasks, h->d_meta, ng, mw_ub + nw_ub, h->stream);
+    pend(h, 5, ev, 2);
+  }
   int err = 0;
   CK(cudaMemcpyAsync(&err, h->d_oz_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->h_counter, h->d_counter, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (err) {
     CK(cudaMemset(h->d_oz_err, 0, sizeof(int)));
     return fail(MPS_ERR_TIMEOUT, "split GEMM: a bounded wait ran out");
   }
+  if (*h->h_counter == 0) return MPS_OK;
   return run_svd(h, ng, nw_ub, 0, false);
 }
 

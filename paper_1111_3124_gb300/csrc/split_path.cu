@@ -12,8 +12,18 @@
 //      small rotation angles keep every column's rounding relative to its own
 //      norm, small singular values included), V2 re-orthonormalised,
 //      B <- B V2 and V <- V V2 by the split-precision GEMM.
-//   6. binary64 Jacobi sweeps on B finish the decomposition (quadratic
-//      convergence from an O(1e-6) start), keeping the column norms, the
+//   6. Gram polish: G = B^H B by the split-precision GEMM (its error is
+//      ~2^-56 sqrt(Mw) |b_p||b_q|, far below the Mw eps |b_p||b_q| that the
+//      test resolves); the binary64 test |g_pq| <= Mw eps sqrt(g_pp g_qq) on
+//      G; from an O(1e-6) start all pair rotations are small and nearly
+//      commute, so one simultaneous step takes the skew-Hermitian X whose
+//      (p,q) entry is the Jacobi angle of the pair's 2 x 2 problem with
+//      g_pq's phase (x_pq ~ g_pq / (g_qq - g_pp)), W = exp(X) to fourth
+//      order, B <- B W (columns balanced by their norms), V <- V W. Three
+//      steps,
+//      then a last Gram test; a task with a near-degenerate pair
+//      (|x_pq| > 1e-3) or still above the tolerance goes on to
+//   7. binary64 blocked Jacobi sweeps on B, which keep the column norms, the
 //      orthogonality test and the rotation angles in binary64.
 // Truncation and the Lambda^-1 rewrite are those of the binary64 path.
 #include "engine.cuh"
@@ -35,8 +45,75 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
     jobs[t] = j;  // M = N = K = 0: nothing to do
     return;
   }
+  if (kind >= kOzAhA && kind <= kOzVW && (!mt.active || mt.hard)) {
+    jobs[t] = j;  // converged, or left to the blocked sweeps
+    return;
+  }
   double2* Vs = (kind & kOzOnV2) ? tk.V2 : tk.V;
+  const int nw = mt.Nw;
   switch (kind & ~kOzOnV2) {
+    case kOzAhA:  // P = A^H A (Nw x Nw, inner Mw)
+      j.a.p = tk.A;
+      j.a.s_r = mt.Mw;
+      j.a.s_k = 1;
+      j.a.conj = 1;
+      j.b.p = tk.A;
+      j.b.s_r = mt.Mw;
+      j.b.s_k = 1;
+      j.M = j.N = nw;
+      j.K = mt.Mw;
+      j.C = tk.P;
+      j.ldc = nw;
+      break;
+    case kOzXX:  // Q = P P
+    case kOzX3:  // V2 = P Q
+      j.a.p = tk.P;
+      j.a.s_r = 1;
+      j.a.s_k = nw;
+      j.b.p = (kind & ~kOzOnV2) == kOzXX ? tk.P : tk.Q;
+      j.b.s_r = nw;
+      j.b.s_k = 1;
+      j.M = j.N = j.K = nw;
+      j.C = (kind & ~kOzOnV2) == kOzXX ? tk.Q : tk.V2;
+      j.ldc = nw;
+      break;
+    case kOzX4:  // T = Q Q
+      j.a.p = tk.Q;
+      j.a.s_r = 1;
+      j.a.s_k = nw;
+      j.b.p = tk.Q;
+      j.b.s_r = nw;
+      j.b.s_k = 1;
+      j.M = j.N = j.K = nw;
+      j.C = tk.T;
+      j.ldc = nw;
+      break;
+    case kOzAW:  // T = (A D^-1)(D P), D = diag(||a_k||) (k_gram_scales): each
+                 // column of the product keeps its rounding relative to its own norm
+      j.a.p = tk.A;
+      j.a.s_r = 1;
+      j.a.s_k = mt.Mw;
+      j.a.kscale = reinterpret_cast<const double*>(tk.V2);
+      j.b.p = tk.P;
+      j.b.s_r = nw;
+      j.b.s_k = 1;
+      j.b.kscale = reinterpret_cast<const double*>(tk.V2) + nw;
+      j.M = mt.Mw;
+      j.N = j.K = nw;
+      j.C = tk.T;
+      j.ldc = mt.Mw;
+      break;
+    case kOzVW:  // Q = V P
+      j.a.p = tk.V;
+      j.a.s_r = 1;
+      j.a.s_k = nw;
+      j.b.p = tk.P;
+      j.b.s_r = nw;
+      j.b.s_k = 1;
+      j.M = j.N = j.K = nw;
+      j.C = tk.Q;
+      j.ldc = nw;
+      break;
     case kOzTheta:  // T = X Y, 2 chi_L x 2 chi_R, inner chi_s
       j.a.p = tk.g0;
       j.a.rb = mt.xl;
@@ -209,6 +286,178 @@ __global__ void k_take_product(const GateTask* tasks, TaskMeta* meta) {
     mt.rotated = 0;
     mt.sweeps = 0;
     mt.maxoff = 0u;
+    mt.hard = 0;
+  }
+}
+
+// ---------------------------------------------------------- Gram polish ---
+
+constexpr double kEps64 = 1.1102230246251565e-16;  // 2^-53
+constexpr double kGramXMax = 1e-3;  // larger first-order rotations: left to the blocked sweeps
+
+__device__ __forceinline__ bool polishing(const TaskMeta& mt) { return !mt.status && mt.active && !mt.hard; }
+
+// sigma[p] = g_pp (the diagonal, kept while P is overwritten by X)
+__global__ void k_gram_diag(const GateTask* tasks, TaskMeta* meta) {
+  const GateTask& tk = tasks[blockIdx.y];
+  TaskMeta& mt = meta[blockIdx.y];
+  if (!polishing(mt)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) mt.nhard = 0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < mt.Nw; p += gridDim.x * blockDim.x)
+    tk.sigma[p] = tk.P[(size_t)p + (size_t)p * mt.Nw].x;
+}
+
+// The binary64 orthogonality test of every pair on G (numerically zero
+// columns, g_jj <= (Mw eps)^2 ||A||_F^2, excluded, as in the blocked sweeps):
+// mt.rotated <- a pair above Mw eps; with form_x, P <- X in place.
+__global__ void k_gram_x(const GateTask* tasks, TaskMeta* meta, int form_x) {
+  const GateTask& tk = tasks[blockIdx.y];
+  TaskMeta& mt = meta[blockIdx.y];
+  if (!polishing(mt)) return;
+  const int nw = mt.Nw;
+  const double tol = (double)mt.Mw * kEps64;
+  const double tiny = tol * tol * mt.frob2;
+  int above = 0, hard = 0;
+  float mx = 0.f;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)nw * nw;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e % nw), q = (int)(e / nw);
+    double2 x = make_double2(0.0, 0.0);
+    if (p != q) {
+      const double app = tk.sigma[p], aqq = tk.sigma[q];
+      const double2 g = tk.P[e];
+      if (app > tiny && aqq > tiny) {
+        const double ratio = hypot(g.x, g.y) / (sqrt(app) * sqrt(aqq));
+        above |= ratio > tol;
+        mx = fmaxf(mx, (float)ratio);
+        // the exact Jacobi angle of the pair's 2 x 2 problem, tan 2t =
+        // 2 |g_pq| / (g_qq - g_pp), with g_pq's phase: exp of the resulting
+        // generator is that pair's rotation (first order in the others)
+        // (the small solution |t| <= pi/4 taken directly, so that an angle
+        // below pi's last bit is not lost to cancellation)
+        const double gabs = hypot(g.x, g.y);
+        if (gabs > 0.0) {
+          const double dd = aqq - app;
+          const double t = 0.5 * atan2(2.0 * gabs, fabs(dd));
+          const double f = (dd < 0.0 ? -t : t) / gabs;
+          x = make_double2(g.x * f, g.y * f);
+        }
+        if (hypot(x.x, x.y) > kGramXMax) {
+          // near-degenerate pair: left out of X and rotated exactly by
+          // k_givens (up to four per task, else the blocked sweeps)
+          if (ratio > tol && p < q) {
+            const int slot = atomicAdd(&mt.nhard, 1);
+            if (slot < 4) {
+              const double t = hypot(x.x, x.y);
+              const double sn = sin(t) / t;
+              mt.hp[slot] = p;
+              mt.hq[slot] = q;
+              mt.hc[slot] = cos(t);
+              mt.hs[slot] = make_double2(x.x * sn, x.y * sn);
+            } else {
+              hard = 1;
+            }
+          }
+          x = make_double2(0.0, 0.0);
+        }
+      }
+    }
+    if (form_x) tk.P[e] = x;
+  }
+  if (__syncthreads_or(above) && threadIdx.x == 0) mt.rotated = 1;
+  if (__syncthreads_or(hard) && threadIdx.x == 0) mt.hard = 1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(&mt.maxoff, __float_as_uint(mx));
+}
+
+// After a Gram test: a task with no pair above the tolerance is done; on the
+// last test every other task is re-armed for the blocked binary64 sweeps and
+// counted in active_count.
+__global__ void k_gram_end(TaskMeta* meta, int ntask, int final_step, int* active_count) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntask) return;
+  TaskMeta& mt = meta[t];
+  if (mt.status || !mt.active) return;
+  if (!mt.hard && !mt.rotated) {
+    mt.active = 0;  // every pair within the tolerance
+  } else if (final_step) {
+    mt.hard = 0;
+    mt.sweeps = 0;
+    atomicAdd(active_count, 1);
+  }
+  mt.rotated = 0;
+  mt.maxoff = 0u;
+}
+
+// P <- exp(X) to fourth order: I + X + X^2/2 + X^3/6 + X^4/24 (X in P, X^2 in
+// Q, X^3 in V2, X^4 in T). Unitary up to |X|^5/120 (< 1e-17 for |X| <= 1e-3)
+// with every entry's rounding relative to its own size: a Newton-Schulz
+// correction through W^H W = I + O(eps) would put an absolute eps on each
+// entry, which the small columns of B W feel relative to their norms.
+__global__ void k_form_w(const GateTask* tasks, const TaskMeta* meta) {
+  const GateTask& tk = tasks[blockIdx.y];
+  const TaskMeta& mt = meta[blockIdx.y];
+  if (!polishing(mt)) return;
+  const int nw = mt.Nw;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)nw * nw;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const double2 x = tk.P[e], x2 = tk.Q[e], x3 = tk.V2[e], x4 = tk.T[e];
+    const double d = (e % nw) == (e / nw) ? 1.0 : 0.0;
+    const double hx = fma(x4.x, 1.0 / 24.0, fma(x3.x, 1.0 / 6.0, 0.5 * x2.x));
+    const double hy = fma(x4.y, 1.0 / 24.0, fma(x3.y, 1.0 / 6.0, 0.5 * x2.y));
+    tk.P[e] = make_double2(d + (x.x + hx), x.y + hy);
+  }
+}
+
+// Column scales of the product A W, in V2 (free after k_form_w): 1/||a_k||
+// then ||a_k|| (1 for numerically zero columns), from the Gram diagonal.
+__global__ void k_gram_scales(const GateTask* tasks, const TaskMeta* meta) {
+  const GateTask& tk = tasks[blockIdx.y];
+  const TaskMeta& mt = meta[blockIdx.y];
+  if (!polishing(mt)) return;
+  const double tol = (double)mt.Mw * kEps64, tiny = tol * tol * mt.frob2;
+  double* sc = reinterpret_cast<double*>(tk.V2);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < mt.Nw; k += gridDim.x * blockDim.x) {
+    const double g = tk.sigma[k];
+    const double d = g > tiny ? sqrt(g) : 1.0;
+    sc[k] = 1.0 / d;
+    sc[mt.Nw + k] = d;
+  }
+}
+
+// The exact Jacobi rotations of the near-degenerate pairs, applied in turn to
+// every row of A and V: columns (p, q) <- (c a_p - conj(s) a_q, s a_p + c a_q)
+// with s = sin t e^{i phi} (the pair's block of exp(X) with its exact angle).
+__global__ void k_givens(const GateTask* tasks, const TaskMeta* meta) {
+  const GateTask& tk = tasks[blockIdx.y];
+  const TaskMeta& mt = meta[blockIdx.y];
+  if (!polishing(mt) || mt.nhard <= 0) return;
+  const int nh = mt.nhard < 4 ? mt.nhard : 4;
+  const int rows = mt.Mw + mt.Nw;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+    double2* M = r < mt.Mw ? tk.A : tk.V;
+    const int ld = r < mt.Mw ? mt.Mw : mt.Nw;
+    const int row = r < mt.Mw ? r : r - mt.Mw;
+    for (int i = 0; i < nh; ++i) {
+      const size_t ip = (size_t)row + (size_t)mt.hp[i] * ld, iq = (size_t)row + (size_t)mt.hq[i] * ld;
+      const double2 a = M[ip], b = M[iq], s = mt.hs[i];
+      const double c = mt.hc[i];
+      M[ip] = make_double2(c * a.x - (s.x * b.x + s.y * b.y), c * a.y - (s.x * b.y - s.y * b.x));
+      M[iq] = make_double2(fma(s.x, a.x, -s.y * a.y) + c * b.x, fma(s.x, a.y, s.y * a.x) + c * b.y);
+    }
+  }
+}
+
+// A <- T and V <- Q after the rotation products
+__global__ void k_take_t(const GateTask* tasks, const TaskMeta* meta) {
+  const GateTask& tk = tasks[blockIdx.y];
+  const TaskMeta& mt = meta[blockIdx.y];
+  if (!polishing(mt)) return;
+  const size_t na = (size_t)mt.Mw * mt.Nw, nv = (size_t)mt.Nw * mt.Nw;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < na + nv; e += (size_t)gridDim.x * blockDim.x) {
+    if (e < na) tk.A[e] = tk.T[e];
+    else tk.V[e - na] = tk.Q[e - na];
   }
 }
 
@@ -239,6 +488,27 @@ void launch_take_q(const GateTask* t, const TaskMeta* m, int ntask, long long el
 }
 void launch_take_product(const GateTask* t, TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
   k_take_product<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m);
+}
+void launch_givens(const GateTask* t, const TaskMeta* m, int ntask, int rows_ub, cudaStream_t st) {
+  k_givens<<<dim3((rows_ub + 255) / 256, ntask), 256, 0, st>>>(t, m);
+}
+void launch_gram_diag(const GateTask* t, TaskMeta* m, int ntask, int nw_ub, cudaStream_t st) {
+  k_gram_diag<<<dim3((nw_ub + 255) / 256, ntask), 256, 0, st>>>(t, m);
+}
+void launch_gram_x(const GateTask* t, TaskMeta* m, int ntask, long long el_ub, int form_x, cudaStream_t st) {
+  k_gram_x<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m, form_x);
+}
+void launch_gram_end(TaskMeta* m, int ntask, int final_step, int* active_count, cudaStream_t st) {
+  k_gram_end<<<(ntask + 127) / 128, 128, 0, st>>>(m, ntask, final_step, active_count);
+}
+void launch_form_w(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
+  k_form_w<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m);
+}
+void launch_gram_scales(const GateTask* t, const TaskMeta* m, int ntask, int nw_ub, cudaStream_t st) {
+  k_gram_scales<<<dim3((nw_ub + 255) / 256, ntask), 256, 0, st>>>(t, m);
+}
+void launch_take_t(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
+  k_take_t<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m);
 }
 
 }  // namespace mpsgb
