@@ -52,7 +52,11 @@ typedef enum {
 typedef enum {
   MPS_PREC_FP64 = 0,   /* native binary64 on the CUDA cores                   */
   MPS_PREC_SPLIT = 1   /* binary64-accurate products from sliced bf16 tensor-
-                          core products (Ozaki scheme), binary64 elsewhere    */
+                          core products (Ozaki scheme); the SVD runs fp32
+                          Jacobi sweeps, then binary64 Gram-polish steps on
+                          split-precision Gram matrices (binary64 angles and
+                          orthogonality test), the blocked binary64 sweeps
+                          as the fallback                                    */
 } mps_prec;
 
 /* SVD of the gate update (mps_set_mode's svd_mode). */
@@ -259,7 +263,8 @@ int mps_diag(mps_handle h, int cap, int* count, int* k, double* discarded, int* 
  * contraction, 2 = truncation and tensor rewrite (norms, truncate, emit),
  * 3 = split-precision products (tensor-core flops), 4 = fp32 Jacobi pair
  * rotations (split mode), 5 = split-mode element-wise steps (gate mix,
- * conversions, Newton-Schulz update). */
+ * conversions, Newton-Schulz update, Gram-polish test, rotation generator and
+ * Givens rotations). */
 int mps_profile(mps_handle h, int enable);
 
 /* Reads the counters of class `kernel`: summed launch durations in ms, the

@@ -51,7 +51,7 @@ constexpr int kMaxSweeps = 60;
 constexpr int kProfKinds = 6;  // see mps_profile in include/mps.h
 constexpr int kSplitMaxCap = kMaxCap;  // the split GEMM chunks K beyond 512
 constexpr int kF32Sweeps = 30;
-constexpr int kGramSteps = 2;  // simultaneous-rotation steps of the split path's Gram polish
+constexpr int kGramSteps = 3;  // simultaneous-rotation steps of the split path's Gram polish
 
 // Memory budget of one batched pass: the tasks of a layer (or of many
 // circuits' layers) are processed in chunks whose workspace fits this.
@@ -453,41 +453,20 @@ int run_split_theta_svd(mps_state* h, int ng, int xl_ub, int x0_ub, int xr_ub, i
   pend(h, 5, ev, 3);
   rc = run_f32_sweeps(h, ng, nw_ub);
   if (rc) return rc;
-  for (int level = 0; level < 2; ++level) {
-    const int v2 = level;  // the second pass builds V2 and folds it into V
-    if (level == 1) {
-      ev = pbeg(h);
-      launch_to_f32(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub + (long long)nw_ub * nw_ub, h->stream);
-      pend(h, 5, ev, 1);
-      rc = run_f32_sweeps(h, ng, nw_ub);
-      if (rc) return rc;
-    }
+  ev = pbeg(h);
+  launch_v_to_f64(h->d_tasks, h->d_meta, ng, (long long)nw_ub * nw_ub, h->stream);
+  pend(h, 5, ev, 1);
+  for (int it = 0; it < 2; ++it) {  // Newton-Schulz: V <- V (3I - V^H V) / 2
+    if ((rc = oz_gemm(h, ng, kOzVhV, nw_ub, nw_ub, nw_ub))) return rc;
+    if ((rc = oz_gemm(h, ng, kOzVP, nw_ub, nw_ub, nw_ub))) return rc;
     ev = pbeg(h);
-    launch_v_to_f64(h->d_tasks, h->d_meta, ng, (long long)nw_ub * nw_ub, v2, h->stream);
+    launch_ns_update(h->d_tasks, h->d_meta, ng, (long long)nw_ub * nw_ub, h->stream);
     pend(h, 5, ev, 1);
-    const int on = v2 ? kOzOnV2 : 0;
-    for (int it = 0; it < 2; ++it) {  // Newton-Schulz: V <- V (3I - V^H V) / 2
-      rc = oz_gemm(h, ng, kOzVhV | on, nw_ub, nw_ub, nw_ub);
-      if (rc) return rc;
-      rc = oz_gemm(h, ng, kOzVP | on, nw_ub, nw_ub, nw_ub);
-      if (rc) return rc;
-      ev = pbeg(h);
-      launch_ns_update(h->d_tasks, h->d_meta, ng, (long long)nw_ub * nw_ub, v2, h->stream);
-      pend(h, 5, ev, 1);
-    }
-    rc = oz_gemm(h, ng, kOzAV | on, mw_ub, nw_ub, nw_ub);
-    if (rc) return rc;
-    ev = pbeg(h);
-    launch_take_product(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub, h->stream);
-    pend(h, 5, ev, 1);
-    if (level == 1) {
-      rc = oz_gemm(h, ng, kOzVV2, nw_ub, nw_ub, nw_ub);
-      if (rc) return rc;
-      ev = pbeg(h);
-      launch_take_q(h->d_tasks, h->d_meta, ng, (long long)nw_ub * nw_ub, h->stream);
-      pend(h, 5, ev, 1);
-    }
   }
+  if ((rc = oz_gemm(h, ng, kOzAV, mw_ub, nw_ub, nw_ub))) return rc;
+  ev = pbeg(h);
+  launch_take_product(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub, h->stream);
+  pend(h, 5, ev, 1);
   // Gram polish: simultaneous first-order rotations from a split-precision
   // Gram, then a last Gram test; what is left goes to the blocked sweeps
   const long long nv = (long long)nw_ub * nw_ub, na = (long long)mw_ub * nw_ub;

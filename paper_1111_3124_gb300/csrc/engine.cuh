@@ -43,9 +43,9 @@ struct GateTask {
   // split-precision workspace (MPS_PREC_SPLIT)
   float2* A32;          // fp32 copy of the working matrix (preconditioning sweeps)
   float2* V32;          // fp32 right rotations
-  double2* P;           // Nw x Nw scratch (V^H V, then V P)
-  double2* Q;
-  double2* V2;          // right factor of the second preconditioning pass
+  double2* P;           // Nw x Nw scratch: V^H V; the Gram polish's G, X, W
+  double2* Q;           // Nw x Nw scratch: V P; X^2; V W
+  double2* V2;          // Nw x Nw scratch: X^3, then the column scales of A W
 };
 
 // Per-task state written and read by kernels only.

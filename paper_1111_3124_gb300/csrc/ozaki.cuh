@@ -42,25 +42,22 @@ struct OzBuffers {
 int ozaki_zgemm(const OzJob* d_jobs, int njobs, int M_ub, int N_ub, int K_ub, int s, OzBuffers& buf, int* d_err,
                 cudaStream_t st);
 
-// Products of the split-precision two-site update (split_path.cu).
-// kOzVhV, kOzVP, kOzAV act on V (first preconditioning pass) or, with
-// kOzOnV2 added, on V2 (second pass); kOzVV2: Q = V V2.
-// Gram polish (tasks still active and without a near-degenerate pair):
-// kOzAhA: P = A^H A; kOzXX: Q = P P; kOzX3: V2 = P Q; kOzX4: T = Q Q;
+// Products of the split-precision two-site update (split_path.cu):
+// kOzTheta: T = X Y (theta); kOzVhV: P = V^H V; kOzVP: Q = V P; kOzAV: T = A V.
+// Gram polish (tasks still active and without an overflow of near-degenerate
+// pairs): kOzAhA: P = A^H A; kOzXX: Q = P P; kOzX3: V2 = P Q; kOzX4: T = Q Q;
 // kOzAW: T = A P; kOzVW: Q = V P.
 enum {
-  kOzTheta = 0, kOzVhV = 1, kOzVP = 2, kOzAV = 3, kOzVV2 = 4,
-  kOzAhA = 5, kOzXX = 6, kOzX3 = 7, kOzX4 = 8, kOzAW = 9, kOzVW = 10,
-  kOzOnV2 = 16
+  kOzTheta = 0, kOzVhV = 1, kOzVP = 2, kOzAV = 3,
+  kOzAhA = 5, kOzXX = 6, kOzX3 = 7, kOzX4 = 8, kOzAW = 9, kOzVW = 10
 };
 struct GateTask;
 struct TaskMeta;
 void launch_oz_jobs(const GateTask* t, const TaskMeta* m, OzJob* jobs, int ntask, int kind, cudaStream_t st);
 void launch_gate_mix2(const GateTask* t, const TaskMeta* m, int ntask, int xl_ub, int xr_ub, cudaStream_t st);
 void launch_to_f32(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
-void launch_v_to_f64(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, int to_v2, cudaStream_t st);
-void launch_ns_update(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, int on_v2, cudaStream_t st);
-void launch_take_q(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
+void launch_v_to_f64(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
+void launch_ns_update(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
 void launch_take_product(const GateTask* t, TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
 void launch_gram_diag(const GateTask* t, TaskMeta* m, int ntask, int nw_ub, cudaStream_t st);
 void launch_givens(const GateTask* t, const TaskMeta* m, int ntask, int rows_ub, cudaStream_t st);

@@ -7,23 +7,19 @@
 //      (rotation angles in binary64): an approximate right factor V32.
 //   3. V = V32 in binary64, re-orthonormalised by two Newton-Schulz steps
 //      V <- V (3 I - V^H V) / 2, products by the split-precision GEMM.
-//   4. B = A V (split-precision GEMM).
-//   5. A second fp32 pass on B (whose columns are nearly orthogonal, so the
-//      small rotation angles keep every column's rounding relative to its own
-//      norm, small singular values included), V2 re-orthonormalised,
-//      B <- B V2 and V <- V V2 by the split-precision GEMM.
-//   6. Gram polish: G = B^H B by the split-precision GEMM (its error is
+//   4. B = A V (split-precision GEMM): columns orthogonal to ~5e-6.
+//   5. Gram polish: G = B^H B by the split-precision GEMM (its error is
 //      ~2^-56 sqrt(Mw) |b_p||b_q|, far below the Mw eps |b_p||b_q| that the
 //      test resolves); the binary64 test |g_pq| <= Mw eps sqrt(g_pp g_qq) on
-//      G; from an O(1e-6) start all pair rotations are small and nearly
-//      commute, so one simultaneous step takes the skew-Hermitian X whose
-//      (p,q) entry is the Jacobi angle of the pair's 2 x 2 problem with
-//      g_pq's phase (x_pq ~ g_pq / (g_qq - g_pp)), W = exp(X) to fourth
-//      order, B <- B W (columns balanced by their norms), V <- V W. Three
-//      steps,
-//      then a last Gram test; a task with a near-degenerate pair
-//      (|x_pq| > 1e-3) or still above the tolerance goes on to
-//   7. binary64 blocked Jacobi sweeps on B, which keep the column norms, the
+//      G; from such a start all pair rotations are small and nearly commute,
+//      so one simultaneous step takes the skew-Hermitian X whose (p,q) entry
+//      is the Jacobi angle of the pair's 2 x 2 problem with g_pq's phase
+//      (x_pq ~ g_pq / (g_qq - g_pp)), W = exp(X) to fourth order,
+//      B <- B W (columns balanced by their norms), V <- V W; a
+//      near-degenerate pair (|x_pq| > 1e-3) is left out of X and rotated by
+//      its exact Jacobi rotation. Three steps, then a last Gram test; a task
+//      still above the tolerance goes on to
+//   6. binary64 blocked Jacobi sweeps on B, which keep the column norms, the
 //      orthogonality test and the rotation angles in binary64.
 // Truncation and the Lambda^-1 rewrite are those of the binary64 path.
 #include "engine.cuh"
@@ -49,9 +45,8 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
     jobs[t] = j;  // converged, or left to the blocked sweeps
     return;
   }
-  double2* Vs = (kind & kOzOnV2) ? tk.V2 : tk.V;
   const int nw = mt.Nw;
-  switch (kind & ~kOzOnV2) {
+  switch (kind) {
     case kOzAhA:  // P = A^H A (Nw x Nw, inner Mw)
       j.a.p = tk.A;
       j.a.s_r = mt.Mw;
@@ -70,11 +65,11 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
       j.a.p = tk.P;
       j.a.s_r = 1;
       j.a.s_k = nw;
-      j.b.p = (kind & ~kOzOnV2) == kOzXX ? tk.P : tk.Q;
+      j.b.p = kind == kOzXX ? tk.P : tk.Q;
       j.b.s_r = nw;
       j.b.s_k = 1;
       j.M = j.N = j.K = nw;
-      j.C = (kind & ~kOzOnV2) == kOzXX ? tk.Q : tk.V2;
+      j.C = kind == kOzXX ? tk.Q : tk.V2;
       j.ldc = nw;
       break;
     case kOzX4:  // T = Q Q
@@ -135,11 +130,11 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
       j.ldc = 2 * mt.xl;
       break;
     case kOzVhV:  // P = V^H V
-      j.a.p = Vs;
+      j.a.p = tk.V;
       j.a.s_r = mt.Nw;
       j.a.s_k = 1;
       j.a.conj = 1;
-      j.b.p = Vs;
+      j.b.p = tk.V;
       j.b.s_r = mt.Nw;
       j.b.s_k = 1;
       j.M = j.N = j.K = mt.Nw;
@@ -147,21 +142,10 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
       j.ldc = mt.Nw;
       break;
     case kOzVP:  // Q = V P
-      j.a.p = Vs;
-      j.a.s_r = 1;
-      j.a.s_k = mt.Nw;
-      j.b.p = tk.P;
-      j.b.s_r = mt.Nw;
-      j.b.s_k = 1;
-      j.M = j.N = j.K = mt.Nw;
-      j.C = tk.Q;
-      j.ldc = mt.Nw;
-      break;
-    case kOzVV2:  // Q = V V2
       j.a.p = tk.V;
       j.a.s_r = 1;
       j.a.s_k = mt.Nw;
-      j.b.p = tk.V2;
+      j.b.p = tk.P;
       j.b.s_r = mt.Nw;
       j.b.s_k = 1;
       j.M = j.N = j.K = mt.Nw;
@@ -172,7 +156,7 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
       j.a.p = tk.A;
       j.a.s_r = 1;
       j.a.s_k = mt.Mw;
-      j.b.p = Vs;
+      j.b.p = tk.V;
       j.b.s_r = mt.Nw;
       j.b.s_k = 1;
       j.M = mt.Mw;
@@ -237,40 +221,28 @@ __global__ void k_to_f32(const GateTask* tasks, const TaskMeta* meta) {
   }
 }
 
-// V (or V2) = binary64(V32)
-__global__ void k_v_to_f64(const GateTask* tasks, const TaskMeta* meta, int to_v2) {
+// V = binary64(V32)
+__global__ void k_v_to_f64(const GateTask* tasks, const TaskMeta* meta) {
   const GateTask& tk = tasks[blockIdx.y];
   const TaskMeta& mt = meta[blockIdx.y];
   if (mt.status) return;
-  double2* V = to_v2 ? tk.V2 : tk.V;
   const size_t nv = (size_t)mt.Nw * mt.Nw;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv; e += (size_t)gridDim.x * blockDim.x) {
     const float2 v = tk.V32[e];
-    V[e] = make_double2((double)v.x, (double)v.y);
+    tk.V[e] = make_double2((double)v.x, (double)v.y);
   }
 }
 
-// Newton-Schulz step V <- (3 V - V (V^H V)) / 2 = 1.5 V - 0.5 Q (on V or V2)
-__global__ void k_ns_update(const GateTask* tasks, const TaskMeta* meta, int on_v2) {
+// Newton-Schulz step V <- (3 V - V (V^H V)) / 2 = 1.5 V - 0.5 Q
+__global__ void k_ns_update(const GateTask* tasks, const TaskMeta* meta) {
   const GateTask& tk = tasks[blockIdx.y];
   const TaskMeta& mt = meta[blockIdx.y];
   if (mt.status) return;
-  double2* V = on_v2 ? tk.V2 : tk.V;
   const size_t nv = (size_t)mt.Nw * mt.Nw;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv; e += (size_t)gridDim.x * blockDim.x) {
-    const double2 v = V[e], q = tk.Q[e];
-    V[e] = make_double2(fma(1.5, v.x, -0.5 * q.x), fma(1.5, v.y, -0.5 * q.y));
+    const double2 v = tk.V[e], q = tk.Q[e];
+    tk.V[e] = make_double2(fma(1.5, v.x, -0.5 * q.x), fma(1.5, v.y, -0.5 * q.y));
   }
-}
-
-// V = Q (after Q = V V2)
-__global__ void k_take_q(const GateTask* tasks, const TaskMeta* meta) {
-  const GateTask& tk = tasks[blockIdx.y];
-  const TaskMeta& mt = meta[blockIdx.y];
-  if (mt.status) return;
-  const size_t nv = (size_t)mt.Nw * mt.Nw;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv; e += (size_t)gridDim.x * blockDim.x)
-    tk.V[e] = tk.Q[e];
 }
 
 // A = T (Mw x Nw) and re-arm the task for binary64 sweeps
@@ -477,14 +449,11 @@ void launch_gate_mix2(const GateTask* t, const TaskMeta* m, int ntask, int xl_ub
 void launch_to_f32(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
   k_to_f32<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m);
 }
-void launch_v_to_f64(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, int to_v2, cudaStream_t st) {
-  k_v_to_f64<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m, to_v2);
+void launch_v_to_f64(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
+  k_v_to_f64<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m);
 }
-void launch_ns_update(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, int on_v2, cudaStream_t st) {
-  k_ns_update<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m, on_v2);
-}
-void launch_take_q(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
-  k_take_q<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m);
+void launch_ns_update(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
+  k_ns_update<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m);
 }
 void launch_take_product(const GateTask* t, TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
   k_take_product<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m);
