@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   __shared__ C chunk[RCH][C2 + 1];
   __shared__ C G[C2][C2 + 1];
   __shared__ C W[C2][C2 + 1];
-  __shared__ double rc_t[C2 / 2], rc_g[C2 / 2], rc_a[C2 / 2], rc_b[C2 / 2];
+  __shared__ double rc_tg[C2 / 2], rc_a[C2 / 2], rc_b[C2 / 2];
   __shared__ R rc_c[C2 / 2];   // cos of the binary64 angle, rounded once to the working type
   __shared__ C rc_se[C2 / 2];  // s e^{i phi}, likewise
   __shared__ int rc_on[C2 / 2];
@@ -469,23 +469,25 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
         rr_pair(C2, ir, tid, pp, qq);
         const double al = (double)G[pp][pp].x, be = (double)G[qq][qq].x;
         const double gx = (double)G[pp][qq].x, gy = (double)G[pp][qq].y;
-        const double gabs = hypot(gx, gy);
-        int on = al > tiny && be > tiny && gabs > 0.0 && gabs > EPS * sqrt(al) * sqrt(be);
+        const double g2 = gx * gx + gy * gy;
+        int on = al > tiny && be > tiny && g2 > 0.0 && g2 > EPS * EPS * al * be;
         rc_on[tid] = on;
         if (on) {
-          // [al ga; conj(ga) be] = D [al g; g be] D^H, D = diag(1, e^{-i phi});
-          // real rotation of the middle matrix (Golub & Van Loan, sym.schur2), in binary64
-          const double zeta = (be - al) / (2.0 * gabs);
-          double t = 1.0 / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          if (zeta < 0) t = -t;
-          const double c = 1.0 / sqrt(1.0 + t * t);
-          const double s = c * t;
+          // [al g; conj(g) be] = D [al |g|; |g| be] D^H, D = diag(e^{i phi}, 1):
+          // the real symmetric Schur rotation of the middle matrix (Golub & Van
+          // Loan, sym.schur2) in binary64, written with one square root:
+          // t = tan = 2 sign(d) |g| / (|d| + sqrt(d^2 + 4|g|^2)), d = be - al,
+          // so t e^{i phi} = 2 sign(d) g / (|d| + sqrt(...)) and t |g| likewise
+          const double d = be - al;
+          const double rD = 1.0 / (fabs(d) + sqrt(fma(d, d, 4.0 * g2)));
+          const double sg = d < 0.0 ? -2.0 * rD : 2.0 * rD;
+          const double tx = sg * gx, ty = sg * gy;
+          const double c = rsqrt(1.0 + (tx * tx + ty * ty));
           rc_c[tid] = (R)c;
-          rc_t[tid] = t;
-          rc_g[tid] = gabs;
+          rc_tg[tid] = sg * g2;  // t |g|
           rc_a[tid] = al;
           rc_b[tid] = be;
-          rc_se[tid] = mkc<C, R>((R)(s * gx / gabs), (R)(s * gy / gabs));  // s e^{i phi}
+          rc_se[tid] = mkc<C, R>((R)(c * tx), (R)(c * ty));  // s e^{i phi}
           any = 1;
           atomicAdd(&nrot, 1);
         }
@@ -527,8 +529,8 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
         rr_pair(C2, ir, tid, pp, qq);
         G[pp][qq] = zero;
         G[qq][pp] = zero;
-        G[pp][pp] = mkc<C, R>((R)(rc_a[tid] - rc_t[tid] * rc_g[tid]), (R)0);
-        G[qq][qq] = mkc<C, R>((R)(rc_b[tid] + rc_t[tid] * rc_g[tid]), (R)0);
+        G[pp][pp] = mkc<C, R>((R)(rc_a[tid] - rc_tg[tid]), (R)0);
+        G[qq][qq] = mkc<C, R>((R)(rc_b[tid] + rc_tg[tid]), (R)0);
       }
       __syncthreads();
     }
