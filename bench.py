@@ -334,10 +334,18 @@ def run_gpu(a):
     d = prof[dom]
     achieved = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else None
     name, bound, peak, src = roof_def[dom]
+    # DRAM bytes per launch from one ncu capture of a saturated chi=256 layer
+    # (profiles/k_jacobi_pair_*_n64_chi256.md), scaled to this run's average
+    # launch by duration (both kernels are ALU-bound: time tracks work)
+    captured = {0: (390.9e6, 2.2237), 4: (137.6e6, 0.2982)}  # class -> (bytes, ms) per launch
+    ms_launch = d["ms"] / max(d["launches"], 1)
+    traffic = captured[dom][0] * ms_launch / captured[dom][1] if dom in captured else None
     roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if achieved else None, "peak_source": src,
             "flops_per_launch": d["flops"] / max(d["launches"], 1),
-            "ms_per_launch": d["ms"] / max(d["launches"], 1), "traffic": None,
+            "ms_per_launch": ms_launch, "traffic": traffic,
+            "traffic_source": "ncu dram__bytes_read+write of a saturated launch, scaled by duration"
+            if traffic is not None else None,
             "share_of_step": d["ms"] / (1e3 * t_step * a.steps)}
     kernels = {name: {"ms_per_step": prof[i]["ms"] / a.steps, "launches_per_step": prof[i]["launches"] / a.steps,
                       "tflops": prof[i]["flops"] / (prof[i]["ms"] / 1e3) / 1e12 if prof[i]["ms"] > 0 else None}
