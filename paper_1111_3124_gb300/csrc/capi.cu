@@ -210,6 +210,12 @@ TaskLayout task_layout(const TaskRef& r, int k, bool split) {
     sz[2] = std::max(4 * cap * cap, m2 * n2) * sizeof(double2);  // partial contraction uses capacity strides
     sz[3] = nw * sizeof(double);
     sz[4] = nw * sizeof(int);
+    if (split) {
+      sz[2] = std::max(sz[2], mw1 * nw1 * sizeof(double2));  // products A V, A W of the first split
+      sz[5] = mw1 * nw1 * sizeof(float2);
+      sz[6] = nw * nw * sizeof(float2);
+      sz[7] = sz[8] = sz[9] = nw * nw * sizeof(double2);
+    }
   } else {
     const size_t m = 2 * xl, n = 2 * xr;
     const size_t mw = std::max(m, n), nw = std::min(m, n);
@@ -442,16 +448,14 @@ int run_f32_sweeps(mps_state* h, int ng, int nw_ub) {
 // Split-precision theta and SVD of a layer of two-site gates (split_path.cu):
 // theta by the split GEMM, fp32 preconditioning sweeps, Newton-Schulz
 // re-orthonormalisation of V and B = A V by the split GEMM, binary64 sweeps.
-int run_split_theta_svd(mps_state* h, int ng, int xl_ub, int x0_ub, int xr_ub, int nw_ub) {
-  const int mw_ub = std::max(2 * xl_ub, 2 * xr_ub);
-  int rc = oz_gemm(h, ng, kOzTheta, 2 * xl_ub, 2 * xr_ub, x0_ub);
-  if (rc) return rc;
+// Split-precision SVD of each task's working matrix in A (Mw x Nw, frob2 set):
+// fp32 sweeps, V re-orthonormalised, B = A V, Gram polish, and the blocked
+// binary64 sweeps for what the polish leaves (split_path.cu).
+int run_split_svd(mps_state* h, int ng, int mw_ub, int nw_ub) {
   int ev = pbeg(h);
-  launch_gate_mix2(h->d_tasks, h->d_meta, ng, xl_ub, xr_ub, h->stream);
-  launch_frob(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub, 0, h->stream);
   launch_to_f32(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub + (long long)nw_ub * nw_ub, h->stream);
-  pend(h, 5, ev, 3);
-  rc = run_f32_sweeps(h, ng, nw_ub);
+  pend(h, 5, ev, 1);
+  int rc = run_f32_sweeps(h, ng, nw_ub);
   if (rc) return rc;
   ev = pbeg(h);
   launch_v_to_f64(h->d_tasks, h->d_meta, ng, (long long)nw_ub * nw_ub, h->stream);
@@ -505,6 +509,19 @@ int run_split_theta_svd(mps_state* h, int ng, int xl_ub, int x0_ub, int xr_ub, i
   }
   if (*h->h_counter == 0) return MPS_OK;
   return run_svd(h, ng, nw_ub, 0, false);
+}
+
+// Two-site split-precision update: theta by the split GEMM and the gate mix,
+// then the split SVD.
+int run_split_theta_svd(mps_state* h, int ng, int xl_ub, int x0_ub, int xr_ub, int nw_ub) {
+  const int mw_ub = std::max(2 * xl_ub, 2 * xr_ub);
+  int rc = oz_gemm(h, ng, kOzTheta, 2 * xl_ub, 2 * xr_ub, x0_ub);
+  if (rc) return rc;
+  const int ev = pbeg(h);
+  launch_gate_mix2(h->d_tasks, h->d_meta, ng, xl_ub, xr_ub, h->stream);
+  launch_frob(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub, 0, h->stream);
+  pend(h, 5, ev, 2);
+  return run_split_svd(h, ng, mw_ub, nw_ub);
 }
 
 // The update pipeline of one pass of k-site gates (k = 2, 3), possibly from
@@ -579,7 +596,7 @@ int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const
   CK(cudaMemcpyAsync(w->d_tasks, w->h_tasks, sizeof(GateTask) * ng, cudaMemcpyHostToDevice, w->stream));
   launch_setup(w->d_tasks, w->d_meta, ng, 0, w->stream);
   w->launches_all += 1;
-  if (split) {
+  if (split && k == 2) {
     rc = run_split_theta_svd(w, ng, xl_ub, x0_ub, xr_ub, nw_ub);
     if (rc) return rc;
   } else {
@@ -590,7 +607,8 @@ int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const
     launch_frob(w->d_tasks, w->d_meta, ng, (long long)(2 * xl_ub) * ((k == 3 ? 4 : 2) * xr_ub), 0, w->stream);
     w->launches_all += 1;
     CK(cudaGetLastError());
-    rc = run_svd(w, ng, nw_ub, 0);
+    // three-site split mode: the binary64 theta (two contraction steps), split SVD
+    rc = split ? run_split_svd(w, ng, std::max(2 * xl_ub, 4 * xr_ub), nw_ub) : run_svd(w, ng, nw_ub, 0);
     if (rc) return rc;
   }
   const int k_ub = std::min(cap_ub, nw_ub);
@@ -626,8 +644,18 @@ int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const
     }
     launch_frob(w->d_tasks, w->d_meta, ng, (long long)(2 * k_ub) * (2 * xr_ub), 1, w->stream);
     w->launches_all += 1;
-    rc = run_svd(w, ng, nw2_ub, 1);
-    if (rc) return rc;
+    if (split) {
+      // the second working matrix (in T) moves to A for the split SVD and back
+      const long long el2 = (long long)(2 * k_ub) * (2 * xr_ub);
+      launch_copy_work(w->d_tasks, w->d_meta, ng, el2, 0, w->stream);
+      rc = run_split_svd(w, ng, std::max(2 * k_ub, 2 * xr_ub), nw2_ub);
+      if (rc) return rc;
+      launch_copy_work(w->d_tasks, w->d_meta, ng, el2, 1, w->stream);
+      w->launches_all += 2;
+    } else {
+      rc = run_svd(w, ng, nw2_ub, 1);
+      if (rc) return rc;
+    }
     const int k2_ub = std::min(cap_ub, nw2_ub);
     ev = pbeg(w);
     launch_colnorms(w->d_tasks, w->d_meta, ng, nw2_ub, 1, w->stream);
@@ -1030,7 +1058,7 @@ int run_refs_chunked(mps_state* w, int k, std::vector<TaskRef>& refs, const doub
     w->svd_mode = saved;
       return rc;
   }
-  bool split = k == 2 && w->prec == MPS_PREC_SPLIT;
+  bool split = (k == 2 || k == 3) && w->prec == MPS_PREC_SPLIT;
   for (const TaskRef& r : refs) split = split && r.st->cap <= kSplitMaxCap;
   size_t g0 = 0;
   while (g0 < refs.size()) {

@@ -61,6 +61,7 @@ void launch_ns_update(const GateTask* t, const TaskMeta* m, int ntask, long long
 void launch_take_product(const GateTask* t, TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
 void launch_gram_diag(const GateTask* t, TaskMeta* m, int ntask, int nw_ub, cudaStream_t st);
 void launch_givens(const GateTask* t, const TaskMeta* m, int ntask, int rows_ub, cudaStream_t st);
+void launch_copy_work(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, int to_t, cudaStream_t st);
 void launch_gram_x(const GateTask* t, TaskMeta* m, int ntask, long long el_ub, int form_x, cudaStream_t st);
 void launch_gram_end(TaskMeta* m, int ntask, int final_step, int* active_count, cudaStream_t st);
 void launch_form_w(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);

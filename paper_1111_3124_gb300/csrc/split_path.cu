@@ -21,6 +21,9 @@
 //      still above the tolerance goes on to
 //   6. binary64 blocked Jacobi sweeps on B, which keep the column norms, the
 //      orthogonality test and the rotation angles in binary64.
+// A three-site update forms theta in binary64 (two contraction steps) and
+// runs steps 2-6 on each of its two splits (the second one's working matrix
+// is copied from T to A and back).
 // Truncation and the Lambda^-1 rewrite are those of the binary64 path.
 #include "engine.cuh"
 #include "kernels.cuh"
@@ -433,6 +436,19 @@ __global__ void k_take_t(const GateTask* tasks, const TaskMeta* meta) {
   }
 }
 
+// Three-site second split: the working matrix (Mw x Nw, column-major) from T
+// to A before the split SVD (to_t = 0) and back after it (to_t = 1).
+__global__ void k_copy_work(const GateTask* tasks, const TaskMeta* meta, int to_t) {
+  const GateTask& tk = tasks[blockIdx.y];
+  const TaskMeta& mt = meta[blockIdx.y];
+  if (mt.status) return;
+  const size_t na = (size_t)mt.Mw * mt.Nw;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < na; e += (size_t)gridDim.x * blockDim.x) {
+    if (to_t) tk.T[e] = tk.A[e];
+    else tk.A[e] = tk.T[e];
+  }
+}
+
 static inline int grid_for(long long el) {
   long long b = (el + 255) / 256;
   if (b > 1024) b = 1024;
@@ -457,6 +473,9 @@ void launch_ns_update(const GateTask* t, const TaskMeta* m, int ntask, long long
 }
 void launch_take_product(const GateTask* t, TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
   k_take_product<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m);
+}
+void launch_copy_work(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, int to_t, cudaStream_t st) {
+  k_copy_work<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m, to_t);
 }
 void launch_givens(const GateTask* t, const TaskMeta* m, int ntask, int rows_ub, cudaStream_t st) {
   k_givens<<<dim3((rows_ub + 255) / 256, ntask), 256, 0, st>>>(t, m);

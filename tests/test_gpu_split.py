@@ -124,3 +124,67 @@ def test_split_single_update_vs_oracle(torch, chi, chi_max):
     assert spectrum_err(gl[1], rl[1]) < 1e-12
     tg, tr = two_site_tensor(gg, gl, 1), two_site_tensor(rg, rl, 1)
     assert np.max(np.abs(tg - tr)) < 1e-11 * np.max(np.abs(tr))
+
+
+# ------------------------------------------------ three-site (U(8)) updates ---
+
+@pytest.mark.parametrize("chi,chi_max", [((1, 9, 13, 11, 7, 1), 128), ((1, 33, 40, 21, 17, 1), 128),
+                                         ((1, 20, 20, 20, 20, 1), 24), ((1, 128, 128, 128, 128, 1), 128)])
+def test_split_three_site_update_vs_oracle(torch, chi, chi_max):
+    """U(8) on sites 1..3 of a 5-site random state in split mode: both splits
+    run the split SVD (the second one's working matrix moved from T to A and
+    back). The third case truncates both splits to chi_max; the last has the
+    three-site workload's chi = 128 shape (theta 256 x 512)."""
+    from tests.helpers import three_site_tensor
+    n = len(chi) - 1
+    state = random_state(n, chi, 7 * sum(chi))
+    U = C.haar_unitary(8, np.random.default_rng(7 * sum(chi) + 1))
+    ref = oracle.OracleMPS(n, chi_max, 1e-12)
+    ref.set_state(*state)
+    ref.apply_gate(1, U)
+    g = split_mps(n, chi_max, 1e-12)
+    g.import_state(*state)
+    g.apply_gate(1, U)
+    _, rg, rl = ref.get_state()
+    _, gg, gl = g.export()
+    for b in (1, 2):
+        assert len(gl[b]) == len(rl[b])
+        assert spectrum_err(gl[b], rl[b]) < 1e-12
+    tg, tr = three_site_tensor(gg, gl, 1), three_site_tensor(rg, rl, 1)
+    assert np.max(np.abs(tg - tr)) < 1e-11 * np.max(np.abs(tr))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_split_mixed_1_2_3_site_gates_vs_statevector(torch, seed):
+    from tests.test_oracle import random_layers
+    rng = np.random.default_rng(300 + seed)
+    n = 8
+    layers = random_layers(n, 6, rng)
+    g = split_mps(n, 64, 0.0)
+    for layer in layers:
+        for site, U in layer:
+            g.apply_gate(site, U)
+    sv = StateVector(n)
+    for layer in layers:
+        for site, U in layer:
+            sv.apply(list(range(site, site + {2: 1, 4: 2, 8: 3}[U.shape[0]])), U)
+    np.testing.assert_allclose(g.amplitudes(all_bits(n)), sv.vector(), atol=1e-10)
+
+
+def test_split_ghz_prefix_and_u8_layers_vs_oracle(torch):
+    """GHZ ladder then two shifted-brick layers of U(8), n = 12, chi_max 32:
+    Schmidt values {1/sqrt 2, 1/sqrt 2} after the prefix, oracle parity after
+    the U(8) layers."""
+    n = 12
+    layers = C.ghz_prefix(n) + C.u8_shifted_brick(n, 2, np.random.default_rng(91))
+    g = split_mps(n, 32, 1e-12)
+    prefix = len(C.ghz_prefix(n))
+    g.run_layers(layers[:prefix])
+    for b in range(n - 1):
+        np.testing.assert_allclose(g.schmidt(b), [2 ** -0.5, 2 ** -0.5], atol=1e-14)
+    g.run_layers(layers[prefix:])
+    ref = oracle_run(n, layers, 32, 1e-12)
+    for b in range(n - 1):
+        assert spectrum_err(g.schmidt(b), ref.schmidt(b)) < 1e-12
+    bits = np.random.default_rng(5).integers(0, 2, size=(64, n)).astype(np.uint8)
+    assert np.max(np.abs(g.amplitudes(bits) - np.array([ref.amplitude(b) for b in bits]))) < 1e-10
