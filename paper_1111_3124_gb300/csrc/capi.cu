@@ -409,13 +409,16 @@ int ensure_oz(mps_state* h, int njobs) {
   return MPS_OK;
 }
 
-int oz_gemm(mps_state* h, int ng, int kind, int M_ub, int N_ub, int K_ub) {
+// slices > 0 caps the slice count of this product (a product that only needs
+// a bounded absolute accuracy); 0 uses the handle's count.
+int oz_gemm(mps_state* h, int ng, int kind, int M_ub, int N_ub, int K_ub, int slices = 0) {
   int rc0 = ensure_oz(h, ng);
   if (rc0) return rc0;
+  const int sl = slices > 0 ? std::min(slices, h->slices) : h->slices;
   launch_oz_jobs(h->d_tasks, h->d_meta, h->d_oz_jobs, ng, kind, h->stream);
   const int ev = pbeg(h);
-  const int rc = ozaki_zgemm(h->d_oz_jobs, ng, M_ub, N_ub, K_ub, h->slices, h->oz_buf, h->d_oz_err, h->stream);
-  const int npair = h->slices * (h->slices + 1) / 2;
+  const int rc = ozaki_zgemm(h->d_oz_jobs, ng, M_ub, N_ub, K_ub, sl, h->oz_buf, h->d_oz_err, h->stream);
+  const int npair = sl * (sl + 1) / 2;
   pend(h, 3, ev, 3, (double)ng * npair * 8.0 * M_ub * N_ub * K_ub);
   h->launches_all += 1;
   if (rc == -2) return fail(MPS_ERR_NOMEM, "split GEMM buffers");
@@ -485,9 +488,12 @@ int run_split_svd(mps_state* h, int ng, int mw_ub, int nw_ub) {
     launch_gram_end(h->d_meta, ng, last ? 1 : 0, h->d_counter, h->stream);
     pend(h, 5, ev, 3);
     if (last) break;
-    if ((rc = oz_gemm(h, ng, kOzXX, nw_ub, nw_ub, nw_ub))) return rc;  // Q = X^2
-    if ((rc = oz_gemm(h, ng, kOzX3, nw_ub, nw_ub, nw_ub))) return rc;  // V2 = X^3
-    if ((rc = oz_gemm(h, ng, kOzX4, nw_ub, nw_ub, nw_ub))) return rc;  // T = X^4
+    // the powers of X need only an absolute accuracy well below 1e-16: with
+    // |x| <= 1e-3 the s-slice error 2^-7s sqrt(Nw) |x|^k stays under 1e-17
+    // for s = 6, 4, 3 (k = 2, 3, 4)
+    if ((rc = oz_gemm(h, ng, kOzXX, nw_ub, nw_ub, nw_ub, 6))) return rc;  // Q = X^2
+    if ((rc = oz_gemm(h, ng, kOzX3, nw_ub, nw_ub, nw_ub, 4))) return rc;  // V2 = X^3
+    if ((rc = oz_gemm(h, ng, kOzX4, nw_ub, nw_ub, nw_ub, 3))) return rc;  // T = X^4
     ev = pbeg(h);
     launch_form_w(h->d_tasks, h->d_meta, ng, nv, h->stream);
     launch_gram_scales(h->d_tasks, h->d_meta, ng, nw_ub, h->stream);
