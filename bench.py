@@ -202,6 +202,26 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ multi-rank ---
+
+def reduce_max(values, world: int):
+    """Max over the ranks of each value: the slowest rank sets the job time.
+    One rank: the values unchanged. NCCL reduces on the device, gloo on the host."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_throughput(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 # ------------------------------------------------------------- GPU arm ---
 
 def run_gpu(a):
@@ -314,12 +334,9 @@ def run_gpu(a):
 
     t_step = sum(times) / len(times) / 1e3
     t_e2e = e2e_s / a.steps
-    if world > 1:
-        tt = torch.tensor([t_step, t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step, t_e2e = float(tt[0]), float(tt[1])
-    value = nup * world / t_step
-    e2e_value = nup * world / t_e2e
+    t_step, t_e2e = reduce_max([t_step, t_e2e], world)
+    value = job_throughput(nup, world, t_step)
+    e2e_value = job_throughput(nup, world, t_e2e)
 
     pk = peaks()
     roof_def = {  # class -> (kernel, bound, peak TFLOP/s, peak source)
