@@ -65,14 +65,16 @@ typedef enum {
   MPS_SVD_SKETCH_MLP = 1  /* rank predicted by an MLP (mps_set_predictor) sizes
                              a randomized range-finder sketch; the full Jacobi
                              SVD is the fallback when the sketch's residual
-                             exceeds the cutoff, and is used directly when the
-                             predicted rank is near the full rank            */
+                             exceeds max(cutoff/100, Mw eps) ||theta||_F, and
+                             is used directly when the sketch width would not
+                             be well below full rank or would reach chi_max  */
 } mps_svd_mode;
 
 /* The rank predictor: a 16-64-1 tanh MLP in fp32 (no paper counterpart: the
  * learned part of this engine). Parameters (1153 floats): W1[64][16],
  * b1[64], w2[64], b2; y = b2 + sum_h w2[h] tanh(b1[h] + sum_i W1[h][i] x_i).
- * The target is log2(kept rank) / 10. */
+ * The target is log2(r) / 10 with r the rank a sketch must capture
+ * (mps_diag's k_sketch). */
 typedef struct mps_mlp* mps_mlp_handle;
 
 /* Creates an MLP on the current device with Glorot-uniform weights drawn from

@@ -726,7 +726,7 @@ OzJob job(OzView a, OzView b, int M, int N, int K, double2* C, long long ldc) {
   return j;
 }
 
-// Predicted kept rank of each two-site gate (features of the current state,
+// Predicted sketch rank of each two-site gate (features of the current state,
 // the MLP forward kernel on the device).
 int predict_ranks(mps_state* w, const std::vector<TaskRef>& refs, const double2* hU, std::vector<double>& rhat) {
   const int n = (int)refs.size();

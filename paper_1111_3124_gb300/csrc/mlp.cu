@@ -1,8 +1,9 @@
 // Learned rank predictor: a 16-64-1 tanh MLP in fp32 with hand-written
 // forward, gradient and Adam kernels, trained on (features of a gate update
-// -> log2 of the rank kept by the truncation) pairs. Its prediction sizes the
+// -> log2 of the rank a sketch must capture: singular values above
+// max(cutoff/100, Mw eps) ||sigma||) pairs. Its prediction sizes the
 // randomized range-finder sketch of the SVD (sketch.cu); the full Jacobi SVD
-// is the fallback and the judge of the sketch.
+// is the fallback, and the sketch's explicit residual decides between them.
 //
 // Parameter layout (kMlpParams floats): W1[64][16] (row = hidden unit),
 // b1[64], w2[64], b2.   y = b2 + sum_h w2[h] tanh(b1[h] + sum_i W1[h][i] x_i)
