@@ -354,7 +354,7 @@ def run_gpu(a):
     # DRAM bytes per launch from one ncu capture of a saturated chi=256 layer
     # (profiles/k_jacobi_pair_*_n64_chi256.md), scaled to this run's average
     # launch by duration (both kernels are ALU-bound: time tracks work)
-    captured = {0: (390.9e6, 2.2237), 4: (137.6e6, 0.2982)}  # class -> (bytes, ms) per launch
+    captured = {0: (390.9e6, 2.2237), 4: (137.7e6, 0.2885)}  # class -> (bytes, ms) per launch
     ms_launch = d["ms"] / max(d["launches"], 1)
     traffic = captured[dom][0] * ms_launch / captured[dom][1] if dom in captured else None
     roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(256) k_jacobi_pair(const GateTask* tasks, Task
   constexpr double EPS = Cx<R>::eps;
   constexpr int C2 = 2 * BW;
   constexpr int NE = C2 * (C2 + 1) / 2;        // Gram entries (p <= q)
-  constexpr int RCH = BW <= 8 ? 64 : 32;       // rows per staged chunk
+  constexpr int RCH = 64;                      // rows per staged chunk
   constexpr int CPT = RCH * C2 / 256;          // rotated outputs per thread (one row, CPT columns)
   static_assert(RCH * C2 == 256 * CPT, "rotation tiling");
   TaskMeta& mt = meta[blockIdx.y];
