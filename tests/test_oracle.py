@@ -309,3 +309,54 @@ def test_numerically_zero_values_dropped_with_zero_cutoff():
     sv = StateVector(4)
     sv.apply([1, 2], U)
     np.testing.assert_allclose(mps_vector(m, 4), sv.vector(), atol=1e-15)
+
+
+def test_schmidt_weights_sum_to_one_after_every_gate():
+    """Eq. (2): every Lambda_b is a unit vector after every update, truncating
+    or not (the kept values are renormalised, Sec. 3.1)."""
+    rng = np.random.default_rng(71)
+    n = 9
+    m = oracle.OracleMPS(n, 6, 1e-3)  # chi_max 6 and a coarse cutoff: every layer truncates
+    for layer in random_layers(n, 8, rng):
+        for site, U in layer:
+            m.apply_gate(site, U)
+            for b in range(n - 1):
+                lam = m.schmidt(b)
+                assert abs(np.sum(lam ** 2) - 1.0) < 1e-14
+                assert np.all(lam > 0) and np.all(np.diff(lam) <= 0)
+
+
+def test_reduced_density_is_a_density_matrix():
+    """RDO (Sec. 3.2) of a truncated state: Hermitian, unit trace, positive
+    semidefinite, for one to four qubits in any listed order."""
+    rng = np.random.default_rng(72)
+    n = 8
+    m = oracle.OracleMPS(n, 8, 1e-6)
+    for layer in random_layers(n, 6, rng):
+        for site, U in layer:
+            m.apply_gate(site, U)
+    for qs in ([3], [6, 1], [0, 4, 7], [5, 2, 3, 0]):
+        rho = m.reduced_density(qs)
+        np.testing.assert_allclose(rho, rho.conj().T, atol=1e-14)
+        assert abs(np.trace(rho) - 1.0) < 1e-13
+        assert np.min(np.linalg.eigvalsh(rho)) > -1e-13
+
+
+def test_ghz_expectations_closed_form():
+    """GHZ_n = (|0..0> + |1..1>)/sqrt 2: <Z_q> = 0, <Z_q Z_q+1> = 1,
+    <X X X> on three neighbours = 0 for n > 3 and 1 for n = 3, and the
+    one-qubit RDO is I/2."""
+    Z = np.diag([1.0, -1.0]).astype(np.complex128)
+    X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+    for n in (3, 7):
+        m = oracle.OracleMPS(n, 4, 1e-12)
+        for layer in C.ghz_prefix(n):
+            for site, U in layer:
+                m.apply_gate(site, U)
+        for q in range(n):
+            assert abs(m.expectation(q, Z)) < 1e-14
+        for q in range(n - 1):
+            assert abs(m.expectation(q, np.kron(Z, Z)) - 1.0) < 1e-14
+        xxx = m.expectation(0, np.kron(np.kron(X, X), X))
+        assert abs(xxx - (1.0 if n == 3 else 0.0)) < 1e-14
+        np.testing.assert_allclose(m.reduced_density([n // 2]), np.eye(2) / 2, atol=1e-15)
