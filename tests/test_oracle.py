@@ -360,3 +360,21 @@ def test_ghz_expectations_closed_form():
         xxx = m.expectation(0, np.kron(np.kron(X, X), X))
         assert abs(xxx - (1.0 if n == 3 else 0.0)) < 1e-14
         np.testing.assert_allclose(m.reduced_density([n // 2]), np.eye(2) / 2, atol=1e-15)
+
+
+def test_echo_brickwork_returns_to_the_initial_state():
+    """The Loschmidt-echo input (weak brickwork, then the layers reversed with
+    U -> U^dagger) is the identity on the state vector, and its forward half
+    entangles (a sanity check of the workload generator, no method arithmetic)."""
+    n = 8
+    layers = C.echo_brickwork(n, 6, np.random.default_rng(73), t_max=0.4)
+    sv = StateVector(n)
+    for layer in layers[:6]:
+        for site, U in layer:
+            sv.apply([site, site + 1], U)
+    assert abs(sv.vector()[0]) < 0.999
+    for layer in layers[6:]:
+        for site, U in layer:
+            sv.apply([site, site + 1], U)
+    v = sv.vector()
+    assert abs(abs(v[0]) - 1.0) < 1e-13 and np.max(np.abs(v[1:])) < 1e-13
