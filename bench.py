@@ -202,6 +202,37 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------- nominal work ---
+
+def nominal_update_flops(chi_l: int, chi_m: int, chi_r: int) -> float:
+    """Nominal binary64 work of one two-site update on bonds (chi_l, chi_m,
+    chi_r): theta as a complex GEMM, 8 flops per multiply-add over
+    (2 chi_l) x (2 chi_r) x chi_m, plus the SVD of the complex M x N theta by
+    the Golub-Reinsch count 4 (14 M N^2 + 8 N^3), M >= N. At chi = 256
+    everywhere: 32 chi^3 + 704 chi^3 = 12.4 GFLOP."""
+    m, n = 2 * chi_l, 2 * chi_r
+    if m < n:
+        m, n = n, m
+    return 8.0 * m * n * chi_m + 4.0 * (14.0 * m * n * n + 8.0 * n ** 3)
+
+
+def step_nominal_flops(m, dev_layers, n: int) -> float:
+    """One untimed pass of the circuit, summing the nominal work of every
+    two-site update from the bond dimensions before its layer."""
+    total = 0.0
+    m.reset()
+    for k, s, dU in dev_layers:
+        if k == 2:
+            bd = m.bond_dims()
+            for site in s.tolist():
+                chi_l = int(bd[site - 1]) if site > 0 else 1
+                chi_r = int(bd[site + 1]) if site + 1 < n - 1 else 1
+                total += nominal_update_flops(chi_l, int(bd[site]), chi_r)
+        m.apply_layer_device(s, dU, k)
+    m.sync()
+    return total
+
+
 # ------------------------------------------------------------ multi-rank ---
 
 def reduce_max(values, world: int):
@@ -263,6 +294,10 @@ def run_gpu(a):
         for _ in range(a.warmup):
             step_device()
         m.sync()
+        try:
+            nominal = step_nominal_flops(m, dev_layers, c["n"])
+        except Exception:  # a diagnostic only: the bench line does not depend on it
+            nominal = None
         chi = m.bond_dims()
         barrier()
         # ---- device-resident timed region
@@ -382,6 +417,15 @@ def run_gpu(a):
     if fp64 is not None:
         fp64["split_speedup"] = value / world / fp64["value"]
         line["fp64_path"] = fp64
+    if nominal:
+        # nominal binary64 work (theta GEMM + Golub-Reinsch SVD count) per second
+        # against the native binary64 peak: the effective binary64 rate of the path
+        line["nominal_binary64"] = {
+            "gflop_per_step": nominal / 1e9, "tflops": nominal / t_step / 1e12,
+            "peak_fp64_tflops": pk["fp64_tflops"], "frac_of_fp64_peak": nominal / t_step / 1e12 / pk["fp64_tflops"],
+            "definition": "per update 8*M*N*chi + 4*(14*M*N^2 + 8*N^3), theta M x N = 2chi_L x 2chi_R"}
+        if fp64 is not None:
+            fp64["nominal_binary64_tflops"] = nominal / (fp64["ms_per_step"] / 1e3) / 1e12
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_obj(a.cpu_sample)
     if rank == 0:

@@ -67,3 +67,42 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = _run_reference({"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_nominal_work_count():
+    """Nominal binary64 work per two-site update: 32 chi^3 (theta) + 704 chi^3
+    (Golub-Reinsch SVD of the complex 2chi x 2chi theta) at square chi; the
+    wide case is counted on its transpose; the pass reads the bonds around
+    each gate (1 at the chain's ends) and skips single-site layers."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    assert bench.nominal_update_flops(256, 256, 256) == 736 * 256 ** 3
+    assert bench.nominal_update_flops(4, 8, 16) == bench.nominal_update_flops(16, 8, 4)
+    m_, n_ = 32, 8  # chi_l = 16, chi_r = 4
+    assert bench.nominal_update_flops(16, 8, 4) == 8 * m_ * n_ * 8 + 4 * (14 * m_ * n_ ** 2 + 8 * n_ ** 3)
+
+    class Stub:  # bond dimensions 2, 3, 5 of a 4-site chain; records the calls
+        def __init__(self):
+            self.calls = []
+
+        def reset(self):
+            self.calls.append("reset")
+
+        def bond_dims(self):
+            return np.array([2, 3, 5], dtype=np.int32)
+
+        def apply_layer_device(self, s, dU, k):
+            self.calls.append((k, tuple(s.tolist())))
+
+        def sync(self):
+            self.calls.append("sync")
+
+    layers = [(2, np.array([0, 2], dtype=np.int32), None), (1, np.array([0, 1, 2, 3], dtype=np.int32), None),
+              (2, np.array([1], dtype=np.int32), None)]
+    stub = Stub()
+    got = bench.step_nominal_flops(stub, layers, 4)
+    want = (bench.nominal_update_flops(1, 2, 3) + bench.nominal_update_flops(3, 5, 1)
+            + bench.nominal_update_flops(2, 3, 5))
+    assert got == want
+    assert stub.calls == ["reset", (2, (0, 2)), (1, (0, 1, 2, 3)), (2, (1,)), "sync"]
