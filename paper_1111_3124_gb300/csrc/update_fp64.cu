@@ -1,4 +1,6 @@
-// Gate-update kernels, native binary64 path.
+// Gate-update kernels of the native binary64 path, and the blocked Jacobi's
+// fp32 variant that the split-precision path (split_path.cu) preconditions
+// with.
 //
 // Steps of one two-site update (Sec. 3.1: a U(4) gate on qubits s, s+1
 // rewrites only Gamma_s, Lambda_s, Gamma_{s+1}; the update follows Vidal,
