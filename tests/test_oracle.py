@@ -298,6 +298,50 @@ def test_single_truncation_fidelity_equals_kept_weight():
     assert abs(f - (1 - w)) < 1e-12
 
 
+def _top_k_projection(psi, n, bond, k):
+    """The normalised projection of psi onto its k leading Schmidt vectors at
+    the cut (0..bond)|(bond+1..n-1), its Schmidt values and the discarded weight."""
+    m = psi.reshape(1 << (bond + 1), -1)
+    u, s, vh = np.linalg.svd(m, full_matrices=False)
+    w = float(np.sum(s[k:] ** 2) / np.sum(s ** 2))
+    proj = (u[:, :k] * s[:k]) @ vh[:k]
+    return proj.reshape(-1) / np.linalg.norm(proj), s, w
+
+
+@pytest.mark.parametrize("seed,chi_max", [(31, 5), (32, 6), (33, 3)])
+def test_three_site_truncation_is_two_successive_schmidt_projections(seed, chi_max):
+    """A U(8) gate (Sec. 1, Sec. 3.1) whose two splits both truncate. From a
+    canonical state the result is psi_2 = P_2 P_1 U psi (renormalised after
+    each projection), P_1 keeping the chi_max leading Schmidt vectors of U psi
+    at the first cut and P_2 those of the renormalised P_1 U psi at the second
+    cut (Eq. 2). Pins both kept spectra, the summed discarded weight and every
+    amplitude: a second split built from unweighted or mis-ordered first-split
+    vectors, a lost renormalisation or a transposed reshape fails here."""
+    rng = np.random.default_rng(seed)
+    n, b = 8, 2
+    layers = C.brickwork(n, 8, rng)
+    exact, sv = run_both(n, layers)
+    U = C.haar_unitary(8, rng)
+    sv.apply([b, b + 1, b + 2], U)
+    psi = sv.vector()
+    psi1, s1, w1 = _top_k_projection(psi, n, b, chi_max)
+    psi2, s2, w2 = _top_k_projection(psi1, n, b + 1, chi_max)
+    assert len(s1) > chi_max and np.sum(s2 > 1e-12) > chi_max  # both splits truncate
+    trunc = oracle.OracleMPS(n, chi_max, 0.0)
+    trunc.set_state(*exact.get_state()[1:])
+    trunc.apply_gate(b, U)
+    d = trunc.last_diag()
+    assert (trunc.bond_dim(b), trunc.bond_dim(b + 1), d["k"]) == (chi_max, chi_max, chi_max)
+    np.testing.assert_allclose(trunc.schmidt(b), s1[:chi_max] / np.linalg.norm(s1[:chi_max]), atol=1e-13)
+    np.testing.assert_allclose(trunc.schmidt(b + 1), s2[:chi_max] / np.linalg.norm(s2[:chi_max]), atol=1e-13)
+    assert abs(d["discarded"] - (w1 + w2)) < 1e-13
+    v = mps_vector(trunc, n)
+    np.testing.assert_allclose(v, psi2, atol=1e-13)
+    assert abs(np.vdot(v, v).real - 1.0) < 1e-13
+    # the first split alone: |<U psi|psi_1>|^2 = 1 - w_1
+    assert abs(abs(np.vdot(psi, psi1)) ** 2 - (1 - w1)) < 1e-13
+
+
 def test_numerically_zero_values_dropped_with_zero_cutoff():
     """Exact zeros of a rank-deficient theta (a product gate on a product
     state) are dropped even with cutoff 0: the bond stays rank one and the
