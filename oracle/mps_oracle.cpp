@@ -18,7 +18,7 @@
 //   * very small Schmidt coefficients are truncated out (Sec. 3.1, after Eq. 2);
 //   * U(8) gates on three consecutive qubits are elementary gates (Sec. 1, Sec. 3.1):
 //     one theta over three sites, split by two successive SVDs.
-// Readings where the paper is silent (all listed in the design notes):
+// Readings where the paper is silent:
 //   * truncation keeps sigma_j > max(cutoff, m eps) * ||sigma||_2 (m = rows of
 //     the Jacobi working matrix, eps the unit roundoff: values at the SVD's
 //     resolution are numerically zero), at most chi_max values, at least one,

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -46,8 +47,6 @@ int fail(int code, const std::string& msg) {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                        \
   } while (0)
 
-constexpr int kMaxSweeps = 60;
-
 constexpr int kProfKinds = 6;  // see mps_profile in include/mps.h
 constexpr int kSplitMaxCap = kMaxCap;  // the split GEMM chunks K beyond 512
 constexpr int kF32Sweeps = 30;
@@ -62,10 +61,42 @@ constexpr int kMaxTasksPerPass = 4096;
 
 void mpsgb::set_error_message(const char* msg) { g_err = msg; }
 
+namespace {
+// mps_debug_fail_alloc: allocations that still succeed before one is refused
+// (-1: the hook is off).
+std::atomic<long long> g_alloc_left{-1};
+
+bool alloc_refused() {
+  long long left = g_alloc_left.load();
+  while (left >= 0) {
+    if (left == 0) return true;
+    if (g_alloc_left.compare_exchange_weak(left, left - 1)) return false;
+  }
+  return false;
+}
+}  // namespace
+
+cudaError_t mpsgb::dev_alloc(void** p, size_t bytes) {
+  if (alloc_refused()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t mpsgb::host_alloc(void** p, size_t bytes) {
+  if (alloc_refused()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(p, bytes);
+}
+
 struct mps_state {
   int n = 0, cap = 0;
   double cutoff = 0.0;
   int prec = MPS_PREC_FP64, slices = 8, svd_mode = 0;
+  int max_sweeps = kMaxSweeps;  // binary64 Jacobi sweep limit (mps_set_limits)
   cudaStream_t own = nullptr, stream = nullptr;
   double2* gamma = nullptr;
   double* lambda = nullptr;
@@ -109,6 +140,10 @@ struct mps_state {
   int oz_cap = 0;
   OzBuffers oz_buf;
   int* d_oz_err = nullptr;
+  // A bounded wait of the split GEMM ran out: asynchronous copies or tensor-core
+  // products may have been abandoned in flight, so the handle's device state is
+  // no longer trusted and every later split-precision product is refused.
+  int oz_timed_out = 0;
 };
 
 namespace {
@@ -168,12 +203,12 @@ int ensure_tasks(mps_state* h, int ntask) {
   cudaFreeHost(h->h_tasks); cudaFreeHost(h->h_gates);
   h->d_tasks = nullptr; h->d_meta = nullptr; h->d_gates = nullptr; h->h_tasks = nullptr; h->h_gates = nullptr;
   h->task_cap = 0;
-  CK(cudaMalloc(&h->d_tasks, sizeof(GateTask) * cap));
-  CK(cudaMalloc(&h->d_meta, sizeof(TaskMeta) * cap));
+  CK(dev_alloc((void**)&h->d_tasks, sizeof(GateTask) * cap));
+  CK(dev_alloc((void**)&h->d_meta, sizeof(TaskMeta) * cap));
   CK(cudaMemset(h->d_meta, 0, sizeof(TaskMeta) * cap));
-  CK(cudaMalloc(&h->d_gates, sizeof(double2) * 64 * cap));
-  CK(cudaMallocHost(&h->h_tasks, sizeof(GateTask) * cap));
-  CK(cudaMallocHost(&h->h_gates, sizeof(double2) * 64 * cap));
+  CK(dev_alloc((void**)&h->d_gates, sizeof(double2) * 64 * cap));
+  CK(host_alloc((void**)&h->h_tasks, sizeof(GateTask) * cap));
+  CK(host_alloc((void**)&h->h_gates, sizeof(double2) * 64 * cap));
   h->task_cap = cap;
   return MPS_OK;
 }
@@ -247,9 +282,9 @@ int ensure_arena(mps_state* w, size_t bytes) {
   cudaFree(w->arena);
   w->arena = nullptr;
   w->arena_bytes = 0;
-  if (cudaMalloc(&w->arena, grow) != cudaSuccess) {
+  if (dev_alloc((void**)&w->arena, grow) != cudaSuccess) {
     cudaGetLastError();
-    CK(cudaMalloc(&w->arena, bytes));
+    CK(dev_alloc((void**)&w->arena, bytes));
     w->arena_bytes = bytes;
     return MPS_OK;
   }
@@ -284,7 +319,8 @@ bool is_unitary(const double* U, int d) {
   return true;
 }
 
-// U' = U (P_site (x) ... (x) P_{site+k-1}) with the held-back single-qubit gates.
+// U' = U (P_site (x) ... (x) P_{site+k-1}) with the held-back single-qubit gates
+// (they stay held back until consume_pending).
 void fold_pending(mps_state* h, int site, int k, const double* U, double2* out) {
   const int d = 1 << k;
   std::vector<cd> P((size_t)d * d, cd(0));
@@ -305,7 +341,12 @@ void fold_pending(mps_state* h, int site, int k, const double* U, double2* out) 
       for (int m = 0; m < d; ++m) acc += cd(U[2 * (r * d + m)], U[2 * (r * d + m) + 1]) * P[(size_t)m * d + c];
       out[r * d + c] = make_double2(acc.real(), acc.imag());
     }
-  for (int j = 0; j < k; ++j) h->has_pend[site + j] = 0;
+}
+
+// The held-back single-qubit gates of a gate's qubits are consumed once the
+// gate's update has been launched; a call that fails before that keeps them.
+void consume_pending(const TaskRef& r, int k) {
+  for (int j = 0; j < k; ++j) r.st->has_pend[r.site + j] = 0;
 }
 
 // Applies every held-back single-qubit gate (before readouts and exports).
@@ -314,10 +355,10 @@ int flush_pending(mps_state* h) {
   for (int s = 0; s < h->n; ++s) cnt += h->has_pend[s];
   if (!cnt) return MPS_OK;
   if (!h->d_site || !h->h_site) {
-    CK(cudaMalloc(&h->d_site, sizeof(SiteTask) * h->n));
-    CK(cudaMalloc(&h->d_site_gates, sizeof(double2) * 4 * h->n));
-    CK(cudaMallocHost(&h->h_site, sizeof(SiteTask) * h->n));
-    CK(cudaMallocHost(&h->h_site_gates, sizeof(double2) * 4 * h->n));
+    CK(dev_alloc((void**)&h->d_site, sizeof(SiteTask) * h->n));
+    CK(dev_alloc((void**)&h->d_site_gates, sizeof(double2) * 4 * h->n));
+    CK(host_alloc((void**)&h->h_site, sizeof(SiteTask) * h->n));
+    CK(host_alloc((void**)&h->h_site_gates, sizeof(double2) * 4 * h->n));
   }
   CK(cudaStreamSynchronize(h->stream));  // pinned staging reuse
   int t = 0;
@@ -362,14 +403,14 @@ int run_svd_on(mps_state* h, const GateTask* dt, TaskMeta* dm, int ntask, int nw
   const int nb = (nw_ub + kBlockW - 1) / kBlockW;
   const int nbe = nb + (nb & 1);
   unsigned long long* fl = h->prof ? h->d_prof_flops : nullptr;
-  for (int sw = 0; sw < kMaxSweeps; ++sw) {
+  for (int sw = 0; sw < h->max_sweeps; ++sw) {
     for (int r = 0; r < nbe - 1; ++r) {
       const int ev = pbeg(h);
       launch_jacobi_round(dt, dm, ntask, r, nbe / 2, second, fl, h->stream);
       pend(h, 0, ev, 1);
     }
     CK(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
-    launch_sweep_end(dm, ntask, kMaxSweeps, h->d_counter, h->stream);
+    launch_sweep_end(dm, ntask, h->max_sweeps, h->d_counter, h->stream);
     h->launches_all += 1;
     CK(cudaMemcpyAsync(h->h_counter, h->d_counter, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -399,11 +440,11 @@ int ensure_oz(mps_state* h, int njobs) {
     cudaFree(h->d_oz_jobs);
     h->d_oz_jobs = nullptr;
     const int cap = std::max(njobs, h->task_cap);
-    CK(cudaMalloc(&h->d_oz_jobs, sizeof(OzJob) * cap));
+    CK(dev_alloc((void**)&h->d_oz_jobs, sizeof(OzJob) * cap));
     h->oz_cap = cap;
   }
   if (!h->d_oz_err) {
-    CK(cudaMalloc(&h->d_oz_err, sizeof(int)));
+    CK(dev_alloc((void**)&h->d_oz_err, sizeof(int)));
     CK(cudaMemset(h->d_oz_err, 0, sizeof(int)));
   }
   return MPS_OK;
@@ -412,6 +453,7 @@ int ensure_oz(mps_state* h, int njobs) {
 // slices > 0 caps the slice count of this product (a product that only needs
 // a bounded absolute accuracy); 0 uses the handle's count.
 int oz_gemm(mps_state* h, int ng, int kind, int M_ub, int N_ub, int K_ub, int slices = 0) {
+  if (h->oz_timed_out) return fail(MPS_ERR_TIMEOUT, "an earlier split GEMM timed out; the handle's device state is not trusted");
   int rc0 = ensure_oz(h, ng);
   if (rc0) return rc0;
   const int sl = slices > 0 ? std::min(slices, h->slices) : h->slices;
@@ -435,7 +477,7 @@ int run_f32_sweeps(mps_state* h, int ng, int nw_ub) {
   for (int sw = 0; sw < kF32Sweeps; ++sw) {
     for (int r = 0; r < nbe - 1; ++r) {
       const int ev = pbeg(h);
-      launch_jacobi_round_f32(h->d_tasks, h->d_meta, ng, r, nbe / 2, fl, h->stream);
+      launch_jacobi_round_f32(h->d_tasks, h->d_meta, ng, r, nbe / 2, kBlockW32, fl, h->stream);
       pend(h, 4, ev, 1);
     }
     CK(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
@@ -510,8 +552,8 @@ int run_split_svd(mps_state* h, int ng, int mw_ub, int nw_ub) {
   CK(cudaMemcpyAsync(h->h_counter, h->d_counter, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (err) {
-    CK(cudaMemset(h->d_oz_err, 0, sizeof(int)));
-    return fail(MPS_ERR_TIMEOUT, "split GEMM: a bounded wait ran out");
+    h->oz_timed_out = 1;  // sticky: see mps_state::oz_timed_out
+    return fail(MPS_ERR_TIMEOUT, "split GEMM: a bounded wait ran out; the handle's device state is not trusted");
   }
   if (*h->h_counter == 0) return MPS_OK;
   return run_svd(h, ng, nw_ub, 0, false);
@@ -689,6 +731,7 @@ int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const
 // Split-precision GEMMs whose jobs are built on the host (exact dimensions).
 int oz_gemm_host(mps_state* w, const std::vector<OzJob>& jobs, int M_ub, int N_ub, int K_ub) {
   if (jobs.empty()) return MPS_OK;
+  if (w->oz_timed_out) return fail(MPS_ERR_TIMEOUT, "an earlier split GEMM timed out; the handle's device state is not trusted");
   const int n = (int)jobs.size();
   int rc0 = ensure_oz(w, n);
   if (rc0) return rc0;
@@ -750,9 +793,9 @@ int predict_ranks(mps_state* w, const std::vector<TaskRef>& refs, const double2*
   }
   FeatureTask* d_ft = nullptr;
   float *d_x = nullptr, *d_y = nullptr;
-  CK(cudaMalloc(&d_ft, sizeof(FeatureTask) * n));
-  CK(cudaMalloc(&d_x, sizeof(float) * 16 * n));
-  CK(cudaMalloc(&d_y, sizeof(float) * n));
+  CK(dev_alloc((void**)&d_ft, sizeof(FeatureTask) * n));
+  CK(dev_alloc((void**)&d_x, sizeof(float) * 16 * n));
+  CK(dev_alloc((void**)&d_y, sizeof(float) * n));
   std::vector<float> y(n);
   cudaError_t e = cudaMemcpyAsync(d_ft, ft.data(), sizeof(FeatureTask) * n, cudaMemcpyHostToDevice, w->stream);
   if (e == cudaSuccess) {
@@ -820,7 +863,7 @@ int run_sketch_pass(mps_state* w, const std::vector<TaskRef>& S, const std::vect
     w->sk_arena = nullptr;
     w->sk_bytes = 0;
     const size_t want = sk_total + 2 * sig_bytes + tab_bytes;
-    CK(cudaMalloc(&w->sk_arena, want));
+    CK(dev_alloc((void**)&w->sk_arena, want));
     w->sk_bytes = want;
   }
   unsigned char* skb = static_cast<unsigned char*>(w->sk_arena);
@@ -1052,6 +1095,10 @@ int run_refs_chunked(mps_state* w, int k, std::vector<TaskRef>& refs, const doub
       std::vector<int> rej;
       rc = run_sketch_pass(w, S, rS, hS.data(), rej);
       if (rc) return rc;
+      std::vector<char> is_rej(S.size(), 0);
+      for (int g : rej) is_rej[g] = 1;
+      for (size_t g = 0; g < S.size(); ++g)
+        if (!is_rej[g]) consume_pending(S[g], 2);
       for (int g : rej) {
         F.push_back(S[g]);
         hF.insert(hF.end(), hS.begin() + 64 * g, hS.begin() + 64 * (g + 1));
@@ -1092,6 +1139,8 @@ int run_refs_chunked(mps_state* w, int k, std::vector<TaskRef>& refs, const doub
     std::vector<TaskRef> part(refs.begin() + g0, refs.begin() + g1);
     rc = run_update_refs(w, k, part, dU, stride, split);
     if (rc) return rc;
+    if (h_U)
+      for (const TaskRef& r : part) consume_pending(r, k);
     g0 = g1;
   }
   return MPS_OK;
@@ -1136,10 +1185,10 @@ int apply_layer_device_impl(mps_state* h, int k, int ng, const int* sites, const
   const int d = 1 << k;
   if (k == 1) {
     if (!h->d_site || !h->h_site) {
-      CK(cudaMalloc(&h->d_site, sizeof(SiteTask) * h->n));
-      CK(cudaMalloc(&h->d_site_gates, sizeof(double2) * 4 * h->n));
-      CK(cudaMallocHost(&h->h_site, sizeof(SiteTask) * h->n));
-      CK(cudaMallocHost(&h->h_site_gates, sizeof(double2) * 4 * h->n));
+      CK(dev_alloc((void**)&h->d_site, sizeof(SiteTask) * h->n));
+      CK(dev_alloc((void**)&h->d_site_gates, sizeof(double2) * 4 * h->n));
+      CK(host_alloc((void**)&h->h_site, sizeof(SiteTask) * h->n));
+      CK(host_alloc((void**)&h->h_site_gates, sizeof(double2) * 4 * h->n));
     }
     CK(cudaStreamSynchronize(h->stream));
     int el_ub = 1;
@@ -1258,8 +1307,8 @@ int rdo_impl(mps_state* h, const int* qubits, int nq, std::vector<cd>& rho) {
   if (e_max > (size_t)1 << 27 || t_max > (size_t)1 << 27) return fail(MPS_ERR_TOO_LARGE, "reduced density too large");
   double2 *E0 = nullptr, *E1 = nullptr, *Tm = nullptr, *Sc = nullptr;
   auto cleanup = [&]() { cudaFree(E0); cudaFree(E1); cudaFree(Tm); cudaFree(Sc); };
-  if (cudaMalloc(&E0, e_max * sizeof(double2)) != cudaSuccess || cudaMalloc(&E1, e_max * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc(&Tm, t_max * sizeof(double2)) != cudaSuccess || cudaMalloc(&Sc, s_max * sizeof(double2)) != cudaSuccess) {
+  if (dev_alloc((void**)&E0, e_max * sizeof(double2)) != cudaSuccess || dev_alloc((void**)&E1, e_max * sizeof(double2)) != cudaSuccess ||
+      dev_alloc((void**)&Tm, t_max * sizeof(double2)) != cudaSuccess || dev_alloc((void**)&Sc, s_max * sizeof(double2)) != cudaSuccess) {
     cleanup();
     return fail(MPS_ERR_NOMEM, "reduced density buffers");
   }
@@ -1349,12 +1398,12 @@ int mps_create(int n, int chi_max, double cutoff, mps_handle* out) {
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
   h->stream = h->own;
-  if ((e = cudaMalloc(&h->gamma, sizeof(double2) * gamma_elems(h))) != cudaSuccess) return bad(e);
-  if ((e = cudaMalloc(&h->lambda, sizeof(double) * (size_t)(n + 1) * chi_max)) != cudaSuccess) return bad(e);
-  if ((e = cudaMalloc(&h->chi, sizeof(int) * (n + 1))) != cudaSuccess) return bad(e);
-  if ((e = cudaMalloc(&h->d_counter, 2 * sizeof(int))) != cudaSuccess) return bad(e);
+  if ((e = dev_alloc((void**)&h->gamma, sizeof(double2) * gamma_elems(h))) != cudaSuccess) return bad(e);
+  if ((e = dev_alloc((void**)&h->lambda, sizeof(double) * (size_t)(n + 1) * chi_max)) != cudaSuccess) return bad(e);
+  if ((e = dev_alloc((void**)&h->chi, sizeof(int) * (n + 1))) != cudaSuccess) return bad(e);
+  if ((e = dev_alloc((void**)&h->d_counter, 2 * sizeof(int))) != cudaSuccess) return bad(e);
   if ((e = cudaMemset(h->d_counter, 0, 2 * sizeof(int))) != cudaSuccess) return bad(e);
-  if ((e = cudaMallocHost(&h->h_counter, sizeof(int))) != cudaSuccess) return bad(e);
+  if ((e = host_alloc((void**)&h->h_counter, sizeof(int))) != cudaSuccess) return bad(e);
   int rc = reset_state(h);
   if (rc) { free_state(h); return rc; }
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bad(e);
@@ -1383,6 +1432,19 @@ int mps_set_mode(mps_handle h, int prec, int slices, int svd_mode) {
   h->prec = prec;
   h->slices = slices ? slices : 8;
   h->svd_mode = svd_mode;
+  return MPS_OK;
+}
+
+int mps_set_limits(mps_handle h, int max_sweeps) {
+  if (!h) return fail(MPS_ERR_ARG, "NULL handle");
+  if (max_sweeps < 1 || max_sweeps > kMaxSweeps) return fail(MPS_ERR_ARG, "max_sweeps must be 1..60");
+  CK(cudaStreamSynchronize(h->stream));
+  h->max_sweeps = max_sweeps;
+  return MPS_OK;
+}
+
+int mps_debug_fail_alloc(long long after) {
+  g_alloc_left.store(after < 0 ? -1 : after);
   return MPS_OK;
 }
 
@@ -1432,8 +1494,8 @@ int mps_layer_features(mps_handle h, int k, int n_gates, const int* sites, const
   }
   FeatureTask* d_ft = nullptr;
   float* d_x = nullptr;
-  CK(cudaMalloc(&d_ft, sizeof(FeatureTask) * n_gates));
-  if (cudaMalloc(&d_x, sizeof(float) * 16 * n_gates) != cudaSuccess) {
+  CK(dev_alloc((void**)&d_ft, sizeof(FeatureTask) * n_gates));
+  if (dev_alloc((void**)&d_x, sizeof(float) * 16 * n_gates) != cudaSuccess) {
     cudaFree(d_ft);
     return fail(MPS_ERR_NOMEM, "feature buffer");
   }
@@ -1465,7 +1527,7 @@ int mps_sketch_stats(mps_handle h, long long* sketched, long long* accepted, lon
 int mps_profile(mps_handle h, int enable) {
   if (!h) return fail(MPS_ERR_ARG, "NULL handle");
   CK(cudaStreamSynchronize(h->stream));
-  if (!h->d_prof_flops) CK(cudaMalloc(&h->d_prof_flops, kProfKinds * sizeof(unsigned long long)));
+  if (!h->d_prof_flops) CK(dev_alloc((void**)&h->d_prof_flops, kProfKinds * sizeof(unsigned long long)));
   CK(cudaMemset(h->d_prof_flops, 0, kProfKinds * sizeof(unsigned long long)));
   h->prof = enable ? 1 : 0;
   h->ev_next = 0;
@@ -1505,8 +1567,8 @@ int mps_amplitudes(mps_handle h, int count, const unsigned char* bits, double* o
   if (rc) return rc;
   unsigned char* d_bits = nullptr;
   double2* d_out = nullptr;
-  CK(cudaMalloc(&d_bits, (size_t)count * h->n));
-  if (cudaMalloc(&d_out, sizeof(double2) * count) != cudaSuccess) {
+  CK(dev_alloc((void**)&d_bits, (size_t)count * h->n));
+  if (dev_alloc((void**)&d_out, sizeof(double2) * count) != cudaSuccess) {
     cudaFree(d_bits);
     return fail(MPS_ERR_NOMEM, "amplitude buffers");
   }

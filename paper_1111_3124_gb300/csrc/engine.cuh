@@ -20,6 +20,7 @@
 namespace mpsgb {
 
 constexpr int kMaxCap = 1024;  // largest chi_max accepted by mps_create
+constexpr int kMaxGivens = 16;  // near-degenerate pairs the Gram polish rotates exactly, per task
 
 // One gate update (k = 2 or 3) of one MPS.
 struct GateTask {
@@ -62,10 +63,10 @@ struct TaskMeta {
   int k1;               // kept rank of the first split (k = 3)
   int ksk;              // singular values above max(cutoff/100, Mw eps) ||sigma||: the rank a sketch must capture
   int hard;             // Gram polish: left to the blocked binary64 sweeps (too many near-degenerate pairs)
-  int nhard;            // Gram polish: near-degenerate pairs found by the last test (rotated exactly, <= 4 kept)
-  int hp[4], hq[4];     //   their columns p < q
-  double hc[4];         //   cos t of the exact Jacobi rotation
-  double2 hs[4];        //   sin t e^{i phi}
+  int nhard;            // Gram polish: near-degenerate pairs found by the last test (rotated exactly, <= kMaxGivens kept)
+  int hp[kMaxGivens], hq[kMaxGivens];  //   their columns p < q
+  double hc[kMaxGivens];               //   cos t of the exact Jacobi rotation
+  double2 hs[kMaxGivens];              //   sin t e^{i phi}
   double disc;          // discarded weight (summed over splits)
   double kept_norm;     // sqrt(sum of kept sigma^2) of the current split
   double frob2;         // ||A||_F^2 of the current working matrix

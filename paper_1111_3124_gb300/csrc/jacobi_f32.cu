@@ -1,0 +1,462 @@
+// The fp32 preconditioning sweep of the split-precision SVD: one launch per
+// round-robin round of the blocked one-sided Jacobi method, one CTA per block
+// pair (I, J) of every task, on the fp32 copies (A32, V32) of the working
+// matrix and of the accumulated right rotations.
+//
+// Per CTA (2b columns, b = BW):
+//   1. Gram G = [A_I A_J]^H [A_I A_J] from 64-row chunks staged in shared
+//      memory (the next chunk is loaded into registers while the current one
+//      is multiplied; one barrier per chunk); 4 x 4 tiles of the upper
+//      triangle, the rows of a chunk split over several threads per tile and
+//      the partial tiles summed in a fixed order.
+//   2. The fp32 test |g_pq| <= 4 sqrt(Mw) eps_32 sqrt(g_pp g_qq) (numerically
+//      zero columns excluded at binary64 resolution); a pair that passes is
+//      left alone.
+//   3. One cyclic sweep of the two-sided Hermitian Jacobi method on G
+//      (circle-method rounds of 2b/2 disjoint rotations). A round is two
+//      barriers: in every warp, lane l forms the rotation of pair l and the
+//      threads take those of their row pair and column pair by shuffle, read
+//      the 2 x 2 block of G those rotations touch, then write J_i^H G_blk J_j
+//      back; the product W of the rotations is accumulated in the same pass.
+//      The rotation of a 2 x 2 Hermitian problem [a g; conj(g) b] is the real
+//      symmetric Schur rotation (Golub & Van Loan) conjugated by
+//      diag(e^{i phi}, 1): t e^{i phi} = 2 sign(d) g / (|d| + sqrt(d^2 + 4|g|^2)),
+//      d = b - a, c = 1 / sqrt(1 + |t|^2), new diagonal a - t|g|, b + t|g|,
+//      formed on the problem scaled by a power of two (see make_rot).
+//   4. [A_I A_J] <- [A_I A_J] W and [V_I V_J] <- [V_I V_J] W, chunk by chunk,
+//      2 x 4 register tiles (W read as 16-byte broadcasts), stores of 32
+//      consecutive rows per warp.
+// The binary64 sweeps that follow (Gram polish, blocked binary64 Jacobi) make
+// the binary64 orthogonality test, so this stage only has to bring the
+// columns close to orthogonal.
+#include "engine.cuh"
+#include "kernels.cuh"
+
+namespace mpsgb {
+
+namespace {
+
+__device__ __forceinline__ float2 f_fma(float2 a, float2 b, float2 acc) {  // acc + a b
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ float2 f_fma_cj(float2 a, float2 b, float2 acc) {  // acc + conj(a) b
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ float2 f_mul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 f_conj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 f_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 f_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 f_scale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+
+// Circle-method pairing of n players (n even), round r, pair p.
+__device__ __forceinline__ void rr_pair_f(int n, int r, int p, int& I, int& J) {
+  if (p == 0) {
+    I = n - 1;
+    J = r;
+  } else {
+    I = (r + p) % (n - 1);
+    J = (r - p + n - 1) % (n - 1);
+  }
+}
+
+// Jacobi rotation of columns (p, q) for the 2 x 2 Hermitian [al g; conj(g) be]:
+// col p' = c col_p - conj(se) col_q, col q' = se col_p + c col_q.
+struct Rot {
+  float c;
+  float2 se;  // s e^{i phi}
+  float tg;   // t |g|: the diagonal moves by -tg (p) and +tg (q)
+  bool on;
+};
+
+// The 2 x 2 problem is first scaled by a power of two to O(1), so that no
+// square of an entry underflows, then the rotation is formed as
+// t e^{i phi} = sg g with sg = 2 sign(d) / (|d| + sqrt(d^2 + 4|g|^2)) and
+// c = 1 / sqrt(1 + |t|^2), with correctly rounded square roots and divisions.
+// This keeps c^2 + |s|^2 - 1 an unbiased rounding error: an approximate
+// reciprocal square root or hypotenuse with a one-sided error would shrink
+// or grow every rotation the same way, and over a sweep the accumulated V
+// would drift from unitary, which the preconditioned columns then inherit.
+__device__ __forceinline__ Rot make_rot(float al, float be, float2 g, float tinyf) {
+  Rot r;
+  r.c = 1.f;
+  r.se = make_float2(0.f, 0.f);
+  r.tg = 0.f;
+  r.on = false;
+  if (!(al > tinyf && be > tinyf)) return r;
+  int e;
+  frexpf(fmaxf(al, be), &e);
+  const float sc = ldexpf(1.f, -e);  // exact
+  const float a = al * sc, b = be * sc, gx = g.x * sc, gy = g.y * sc;
+  const float g2 = fmaf(gx, gx, gy * gy);
+  // |g| > eps_32 sqrt(a b)
+  if (!(g2 > 0.f && g2 > (3.5527137e-15f * a) * b)) return r;
+  r.on = true;
+  const float d = b - a;
+  const float sg = (d < 0.f ? -2.f : 2.f) / (fabsf(d) + sqrtf(fmaf(d, d, 4.f * g2)));
+  const float tx = sg * gx, ty = sg * gy;
+  r.c = 1.f / sqrtf(1.f + fmaf(tx, tx, ty * ty));
+  r.se = make_float2(r.c * tx, r.c * ty);
+  r.tg = ldexpf(sg * g2, e);  // t |g| in the original scale
+  return r;
+}
+
+__device__ __forceinline__ Rot shfl_rot(const Rot& r, int src) {
+  Rot o;
+  o.c = __shfl_sync(0xffffffffu, r.c, src);
+  o.se.x = __shfl_sync(0xffffffffu, r.se.x, src);
+  o.se.y = __shfl_sync(0xffffffffu, r.se.y, src);
+  o.tg = __shfl_sync(0xffffffffu, r.tg, src);
+  o.on = __shfl_sync(0xffffffffu, (int)r.on, src) != 0;
+  return o;
+}
+
+constexpr int kRch = 64;  // rows per staged chunk
+
+// Shared memory of one CTA (dynamic: above the 48 KB static limit).
+template <int BW>
+struct JacobiSmem {
+  static constexpr int C2 = 2 * BW, NP = BW, LD = C2 + 1;
+  float2 buf[2][kRch][LD];          // staged chunks; the Gram's partial tiles
+  float2 G[C2][LD];                 // Gram of the block pair
+  float2 W[C2][C2];                 // accumulated rotation (16-byte rows)
+  unsigned char prs[C2 - 1][NP][2];  // inner circle-method pairs
+  int cols[C2];
+  int need, nrot;
+  unsigned int smax;
+};
+
+}  // namespace
+
+template <int BW>
+__global__ void __launch_bounds__(256, 3)
+    k_jacobi_pair_f32(const GateTask* tasks, TaskMeta* meta, int round, unsigned long long* flops) {
+  constexpr int C2 = 2 * BW;                // columns of a block pair
+  constexpr int NP = C2 / 2;                // disjoint rotations per inner round
+  constexpr int RCH = kRch;
+  constexpr int LD = C2 + 1;                // padded chunk row, in float2
+  constexpr int PER = RCH * C2 / 256;       // staged elements per thread
+  constexpr int TB = C2 / 4;                // 4 x 4 Gram tiles per dimension
+  constexpr int NT = TB * (TB + 1) / 2;     // upper-triangle tiles
+  constexpr int RED = 2 * RCH * LD / 16;    // partial tiles the chunk buffers hold
+  constexpr int NPART0 = 256 / NT;
+  constexpr int NPART = NPART0 * NT <= RED ? NPART0 : RED / NT;  // threads per tile
+  constexpr int NCG = C2 / 4;               // rotation: column groups of 4
+  constexpr int SLOTS = 256 / NCG;          // rotation: row slots
+  constexpr int TR = RCH / SLOTS;           // rotation: rows per thread and chunk
+  static_assert(NP * NP <= 256 && RCH * C2 % 256 == 0 && RCH % SLOTS == 0, "tiling");
+  static_assert(NPART >= 1, "Gram tiling");
+  static_assert(NP * NP % 32 == 0 && NP <= 32, "2 x 2 blocks fill whole warps");
+
+  TaskMeta& mt = meta[blockIdx.y];
+  if (!mt.active) return;
+  const GateTask& tk = tasks[blockIdx.y];
+  const int Mw = mt.Mw, Nw = mt.Nw;
+  const int nb = (Nw + BW - 1) / BW;
+  const int nbe = nb + (nb & 1);
+  if (round >= nbe - 1 || (int)blockIdx.x >= nbe / 2) return;
+  int I, J;
+  rr_pair_f(nbe, round, blockIdx.x, I, J);
+  float2* const A = tk.A32;
+  float2* const Vm = tk.V32;
+  const float2 zero = make_float2(0.f, 0.f);
+
+  extern __shared__ __align__(16) unsigned char jsm_raw[];
+  JacobiSmem<BW>& S = *reinterpret_cast<JacobiSmem<BW>*>(jsm_raw);
+  int* const cols = S.cols;
+  auto& buf = S.buf;
+  auto& G = S.G;
+  auto& W = S.W;
+  auto& prs = S.prs;
+  int& need = S.need;
+  int& nrot = S.nrot;
+  unsigned int& smax = S.smax;
+  const int tid = threadIdx.x;
+  if (tid < C2) {
+    const int blk = tid < BW ? I : J;
+    const int j = blk * BW + (tid % BW);
+    cols[tid] = (blk < nb && j < Nw) ? j : -1;
+  }
+  for (int e = tid; e < (C2 - 1) * NP; e += 256) {
+    int p, q;
+    rr_pair_f(C2, e / NP, e % NP, p, q);
+    prs[e / NP][e % NP][0] = (unsigned char)p;
+    prs[e / NP][e % NP][1] = (unsigned char)q;
+  }
+  if (tid == 0) {
+    need = 0;
+    nrot = 0;
+    smax = 0u;
+  }
+  __syncthreads();
+
+  // ---- 1. Gram of the 2b columns
+  float2 pf[PER];
+  auto fetch = [&](const float2* M, int rows, int r0) {
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int e = tid + 256 * j, col = e / RCH, row = e % RCH;
+      const int gc = cols[col];
+      pf[j] = (gc >= 0 && r0 + row < rows) ? M[(size_t)(r0 + row) + (size_t)gc * rows] : zero;
+    }
+  };
+  auto stash = [&](int b) {
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int e = tid + 256 * j;
+      buf[b][e % RCH][e / RCH] = pf[j];
+    }
+  };
+  const int gtile = tid / NPART, gpart = tid % NPART;
+  int ti = 0, tj = 0;
+  if (gtile < NT) {
+    int rem = gtile;
+    while (rem >= TB - ti) {
+      rem -= TB - ti;
+      ++ti;
+    }
+    tj = ti + rem;
+  }
+  float2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = zero;
+  const int nch_a = (Mw + RCH - 1) / RCH;
+  fetch(A, Mw, 0);
+  stash(0);
+  __syncthreads();
+  for (int ch = 0; ch < nch_a; ++ch) {
+    if (ch + 1 < nch_a) fetch(A, Mw, (ch + 1) * RCH);
+    if (gtile < NT) {
+      const int rmax = min(RCH, Mw - ch * RCH);
+      for (int row = gpart; row < rmax; row += NPART) {
+        float2 x[4], y[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          x[a] = buf[ch & 1][row][4 * ti + a];
+          y[a] = buf[ch & 1][row][4 * tj + a];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = f_fma_cj(x[a], y[b], acc[a][b]);
+      }
+    }
+    if (ch + 1 < nch_a) stash((ch + 1) & 1);
+    __syncthreads();
+  }
+  // partial tiles -> G (fixed summation order over the parts)
+  float2* red = &buf[0][0][0];
+  if (gtile < NT) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) red[(gtile * NPART + gpart) * 16 + a * 4 + b] = acc[a][b];
+  }
+  __syncthreads();
+  for (int e = tid; e < NT * 16; e += 256) {
+    const int tile = e / 16, ent = e % 16;
+    int ri = 0, rem = tile;
+    while (rem >= TB - ri) {
+      rem -= TB - ri;
+      ++ri;
+    }
+    const int rj = ri + rem;
+    float2 s = zero;
+    for (int part = 0; part < NPART; ++part) s = f_add(s, red[(tile * NPART + part) * 16 + ent]);
+    const int p = 4 * ri + ent / 4, q = 4 * rj + ent % 4;
+    if (p < q) {
+      G[p][q] = s;
+      G[q][p] = f_conj(s);
+    } else if (p == q) {
+      G[p][p] = make_float2(s.x, 0.f);
+    }
+  }
+  for (int e = tid; e < C2 * C2; e += 256) W[e / C2][e % C2] = make_float2((e / C2) == (e % C2) ? 1.f : 0.f, 0.f);
+  __syncthreads();
+
+  // ---- 2. test (binary64 zero threshold, fp32 resolution)
+  const float tolc = (float)(4.0 * sqrt((double)Mw) * 5.9604644775390625e-08);
+  const float tinyf = (float)((double)Mw * 1.1102230246251565e-16 * (double)Mw * 1.1102230246251565e-16 * mt.frob2);
+  {
+    float mx = 0.f;
+    int nd = 0;
+    for (int e = tid; e < C2 * C2; e += 256) {
+      const int p = e / C2, q = e % C2;
+      if (p >= q) continue;
+      const float al = G[p][p].x, be = G[q][q].x;
+      if (al > tinyf && be > tinyf) {
+        const float ratio = hypotf(G[p][q].x, G[p][q].y) * (rsqrtf(al) * rsqrtf(be));
+        nd |= ratio > tolc;
+        mx = fmaxf(mx, ratio);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0 && mx > 0.f) atomicMax(&smax, __float_as_uint(mx));
+    if (__syncthreads_or(nd) && tid == 0) need = 1;
+  }
+  __syncthreads();
+  if (tid == 0 && smax) atomicMax(&mt.maxoff, smax);
+  int nv = 0;
+  for (int c = 0; c < C2; ++c) nv += cols[c] >= 0;
+  if (!need) {
+    if (flops && tid == 0) atomicAdd(flops, 4ull * nv * (nv + 1) * (unsigned long long)Mw);
+    return;
+  }
+
+  // ---- 3. one cyclic sweep of the Hermitian Jacobi method on G, W = product of the rotations
+  const int bi = tid / NP, bj = tid % NP;  // row pair, column pair of this thread's 2 x 2 block
+  const int lane = tid & 31;
+  const bool blk_warp = (tid & ~31) < NP * NP;  // warps holding 2 x 2 blocks (NP * NP is a multiple of 32)
+  for (int ir = 0; ir < C2 - 1; ++ir) {
+    Rot ri = {1.f, zero, 0.f, false}, rj = ri;
+    int Pi = 0, Qi = 0, Pj = 0, Qj = 0;
+    float2 x00 = zero, x01 = zero, x10 = zero, x11 = zero;
+    float2 w[2][2] = {{zero, zero}, {zero, zero}};
+    if (blk_warp) {  // warp-uniform
+      // lane l < NP forms the rotation of pair l (every block warp forms all
+      // of them, then takes its row and column pairs' by shuffle)
+      Rot mine = {1.f, zero, 0.f, false};
+      if (lane < NP) {
+        const int Pl = prs[ir][lane][0], Ql = prs[ir][lane][1];
+        mine = make_rot(G[Pl][Pl].x, G[Ql][Ql].x, G[Pl][Ql], tinyf);
+      }
+      ri = shfl_rot(mine, bi % 32);
+      rj = shfl_rot(mine, bj);
+      Pi = prs[ir][bi % NP][0];
+      Qi = prs[ir][bi % NP][1];
+      Pj = prs[ir][bj][0];
+      Qj = prs[ir][bj][1];
+      if (tid < NP * NP) {
+        x00 = G[Pi][Pj];
+        x01 = G[Pi][Qj];
+        x10 = G[Qi][Pj];
+        x11 = G[Qi][Qj];
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+          w[m][0] = W[bi + NP * m][Pj];
+          w[m][1] = W[bi + NP * m][Qj];
+        }
+      }
+    }
+    __syncthreads();
+    if (tid < NP * NP) {
+      if (bi == bj) {
+        if (ri.on) {
+          G[Pi][Pi] = make_float2(x00.x - ri.tg, 0.f);
+          G[Qi][Qi] = make_float2(x11.x + ri.tg, 0.f);
+          G[Pi][Qi] = zero;
+          G[Qi][Pi] = zero;
+          atomicAdd(&nrot, 1);
+        }
+      } else if (ri.on || rj.on) {
+        // rows: Y = J_i^H X (row P' = c X_P - se X_Q, row Q' = conj(se) X_P + c X_Q)
+        const float2 y00 = f_sub(f_scale(ri.c, x00), f_mul(ri.se, x10));
+        const float2 y01 = f_sub(f_scale(ri.c, x01), f_mul(ri.se, x11));
+        const float2 y10 = f_add(f_mul(f_conj(ri.se), x00), f_scale(ri.c, x10));
+        const float2 y11 = f_add(f_mul(f_conj(ri.se), x01), f_scale(ri.c, x11));
+        // columns: Z = Y J_j (col P' = c Y_P - conj(se) Y_Q, col Q' = se Y_P + c Y_Q)
+        G[Pi][Pj] = f_sub(f_scale(rj.c, y00), f_mul(f_conj(rj.se), y01));
+        G[Qi][Pj] = f_sub(f_scale(rj.c, y10), f_mul(f_conj(rj.se), y11));
+        G[Pi][Qj] = f_add(f_mul(rj.se, y00), f_scale(rj.c, y01));
+        G[Qi][Qj] = f_add(f_mul(rj.se, y10), f_scale(rj.c, y11));
+      }
+      if (rj.on) {
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+          W[bi + NP * m][Pj] = f_sub(f_scale(rj.c, w[m][0]), f_mul(f_conj(rj.se), w[m][1]));
+          W[bi + NP * m][Qj] = f_add(f_mul(rj.se, w[m][0]), f_scale(rj.c, w[m][1]));
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- 4. [A_I A_J] W and [V_I V_J] W
+  const int slot = tid % SLOTS, cg = tid / SLOTS;
+  const int nch_v = (Nw + RCH - 1) / RCH;
+  const int nch = nch_a + nch_v;
+  fetch(A, Mw, 0);
+  stash(0);
+  __syncthreads();
+  for (int ch = 0; ch < nch; ++ch) {
+    const bool isA = ch < nch_a;
+    float2* const M = isA ? A : Vm;
+    const int rows = isA ? Mw : Nw;
+    const int r0 = (isA ? ch : ch - nch_a) * RCH;
+    if (ch + 1 < nch) {
+      const bool nA = ch + 1 < nch_a;
+      fetch(nA ? A : Vm, nA ? Mw : Nw, (nA ? ch + 1 : ch + 1 - nch_a) * RCH);
+    }
+    float2 o[TR][4];
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) o[r][c] = zero;
+#pragma unroll 8
+    for (int k = 0; k < C2; ++k) {
+      const float4 w01 = *reinterpret_cast<const float4*>(&W[k][4 * cg]);
+      const float4 w23 = *reinterpret_cast<const float4*>(&W[k][4 * cg + 2]);
+      const float2 wv[4] = {make_float2(w01.x, w01.y), make_float2(w01.z, w01.w), make_float2(w23.x, w23.y),
+                            make_float2(w23.z, w23.w)};
+#pragma unroll
+      for (int r = 0; r < TR; ++r) {
+        const float2 x = buf[ch & 1][slot + SLOTS * r][k];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) o[r][c] = f_fma(x, wv[c], o[r][c]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+      const int row = r0 + slot + SLOTS * r;
+      if (row < rows) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int gc = cols[4 * cg + c];
+          if (gc >= 0) M[(size_t)row + (size_t)gc * rows] = o[r][c];
+        }
+      }
+    }
+    if (ch + 1 < nch) stash((ch + 1) & 1);
+    __syncthreads();
+  }
+  if (tid == 0) {
+    mt.rotated = 1;
+    if (flops)
+      atomicAdd(flops, 4ull * nv * (nv + 1) * (unsigned long long)Mw + 60ull * C2 * (unsigned long long)nrot +
+                           8ull * nv * C2 * (unsigned long long)(Mw + Nw));
+  }
+}
+
+template <int BW>
+static void launch_pair_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub,
+                            unsigned long long* flops, cudaStream_t st) {
+  static bool attr = false;
+  constexpr int bytes = (int)sizeof(JacobiSmem<BW>);
+  if (!attr) {
+    cudaFuncSetAttribute(k_jacobi_pair_f32<BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    attr = true;
+  }
+  k_jacobi_pair_f32<BW><<<dim3(pairs_ub, ntask), 256, bytes, st>>>(t, m, round, flops);
+}
+
+void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub, int bw,
+                             unsigned long long* flops, cudaStream_t st) {
+  if (bw == 8)
+    launch_pair_f32<8>(t, m, ntask, round, pairs_ub, flops, st);
+  else
+    launch_pair_f32<16>(t, m, ntask, round, pairs_ub, flops, st);
+}
+
+}  // namespace mpsgb

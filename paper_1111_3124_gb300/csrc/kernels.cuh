@@ -9,9 +9,16 @@ constexpr int kBlockW32 = 16;  // block width of the fp32 preconditioning sweeps
 constexpr float kQuadStop = 1e-8f;  // binary64 sweeps stop after one whose max scaled off-diagonal < this
 constexpr int kInnerSweepsFar = 1;  // inner sweeps of a block pair whose off-diagonal is above kQuadStop ...
 constexpr int kInnerFarSweeps = 30;  // ... during a task's first sweeps
+constexpr int kMaxSweeps = 60;       // binary64 sweep limit of one SVD (MPS_ERR_NOCONVERGE beyond it)
 
 // Sets the message returned by mps_last_error() on the calling thread.
 void set_error_message(const char* msg);
+
+// Every device and pinned-host allocation of the library goes through these,
+// so that a test can make the n-th one fail (mps_debug_fail_alloc) and check
+// the MPS_ERR_NOMEM path without exhausting a shared GPU.
+cudaError_t dev_alloc(void** p, size_t bytes);
+cudaError_t host_alloc(void** p, size_t bytes);
 
 void launch_setup(const GateTask* t, TaskMeta* m, int ntask, int stage, cudaStream_t st);
 void launch_contract2(const GateTask* t, const TaskMeta* m, int ntask, int a_ub, int b_ub, cudaStream_t st);
@@ -23,7 +30,8 @@ void launch_jacobi_round(const GateTask* t, TaskMeta* m, int ntask, int round, i
                          unsigned long long* flops, cudaStream_t st);
 void launch_sweep_end(TaskMeta* m, int ntask, int max_sweeps, int* active_count, cudaStream_t st);
 void launch_sweep_end_nofail(TaskMeta* m, int ntask, int max_sweeps, int* active_count, cudaStream_t st);
-void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub,
+// fp32 preconditioning round (jacobi_f32.cu), block width bw = 8 or 16.
+void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub, int bw,
                              unsigned long long* flops, cudaStream_t st);
 void launch_colnorms(const GateTask* t, const TaskMeta* m, int ntask, int nw_ub, int second, cudaStream_t st);
 void launch_truncate(const GateTask* t, TaskMeta* m, int ntask, int stage, int chi_cap, cudaStream_t st);

@@ -189,9 +189,9 @@ int mps_mlp_create(unsigned long long seed, mps_mlp_handle* out) {
   *out = nullptr;
   mps_mlp* m = new mps_mlp();
   const size_t bytes = sizeof(float) * kMlpParams;
-  if (cudaMalloc(&m->P, bytes) != cudaSuccess || cudaMalloc(&m->G, bytes) != cudaSuccess ||
-      cudaMalloc(&m->M, bytes) != cudaSuccess || cudaMalloc(&m->V, bytes) != cudaSuccess ||
-      cudaMalloc(&m->d_loss, sizeof(float)) != cudaSuccess) {
+  if (dev_alloc((void**)&m->P, bytes) != cudaSuccess || dev_alloc((void**)&m->G, bytes) != cudaSuccess ||
+      dev_alloc((void**)&m->M, bytes) != cudaSuccess || dev_alloc((void**)&m->V, bytes) != cudaSuccess ||
+      dev_alloc((void**)&m->d_loss, sizeof(float)) != cudaSuccess) {
     mps_mlp_destroy(m);
     return mfail(MPS_ERR_NOMEM, "MLP buffers");
   }
@@ -238,7 +238,7 @@ int mps_mlp_forward(mps_mlp_handle m, int B, const float* X, float* Y) {
   if (!m || B < 0 || (B > 0 && (!X || !Y))) return mfail(MPS_ERR_ARG, "bad arguments");
   if (B == 0) return MPS_OK;
   float *dX = nullptr, *dY = nullptr;
-  if (cudaMalloc(&dX, sizeof(float) * kMlpIn * B) != cudaSuccess || cudaMalloc(&dY, sizeof(float) * B) != cudaSuccess) {
+  if (dev_alloc((void**)&dX, sizeof(float) * kMlpIn * B) != cudaSuccess || dev_alloc((void**)&dY, sizeof(float) * B) != cudaSuccess) {
     cudaFree(dX);
     return mfail(MPS_ERR_NOMEM, "MLP batch");
   }
@@ -255,7 +255,7 @@ int mps_mlp_forward(mps_mlp_handle m, int B, const float* X, float* Y) {
 int mps_mlp_loss_grad(mps_mlp_handle m, int B, const float* X, const float* T, float* loss, float* grad) {
   if (!m || B < 1 || !X || !T) return mfail(MPS_ERR_ARG, "bad arguments");
   float *dX = nullptr, *dT = nullptr;
-  if (cudaMalloc(&dX, sizeof(float) * kMlpIn * B) != cudaSuccess || cudaMalloc(&dT, sizeof(float) * B) != cudaSuccess) {
+  if (dev_alloc((void**)&dX, sizeof(float) * kMlpIn * B) != cudaSuccess || dev_alloc((void**)&dT, sizeof(float) * B) != cudaSuccess) {
     cudaFree(dX);
     return mfail(MPS_ERR_NOMEM, "MLP batch");
   }
@@ -279,8 +279,8 @@ int mps_mlp_train(mps_mlp_handle m, int N, const float* X, const float* T, int e
   if (!m || N < 1 || !X || !T || epochs < 1 || batch < 1 || !(lr > 0.f)) return mfail(MPS_ERR_ARG, "bad arguments");
   float *dX = nullptr, *dT = nullptr;
   int* dI = nullptr;
-  if (cudaMalloc(&dX, sizeof(float) * kMlpIn * N) != cudaSuccess || cudaMalloc(&dT, sizeof(float) * N) != cudaSuccess ||
-      cudaMalloc(&dI, sizeof(int) * N) != cudaSuccess) {
+  if (dev_alloc((void**)&dX, sizeof(float) * kMlpIn * N) != cudaSuccess || dev_alloc((void**)&dT, sizeof(float) * N) != cudaSuccess ||
+      dev_alloc((void**)&dI, sizeof(int) * N) != cudaSuccess) {
     cudaFree(dX);
     cudaFree(dT);
     return mfail(MPS_ERR_NOMEM, "training set");

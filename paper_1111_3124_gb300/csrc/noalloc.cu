@@ -13,6 +13,7 @@
 // scratch comes from the static array instead of the handle's workspace.
 #include <cuda_runtime.h>
 
+#include <cstdio>
 #include <mutex>
 
 #include "../../include/mps.h"
@@ -52,6 +53,13 @@ unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};
 int fail_msg(int code, const char* msg) {
   set_error_message(msg);
   return code;
+}
+
+// A failed CUDA call: MPS_ERR_CUDA with the step and the runtime's message.
+int fail_cuda(const char* step, cudaError_t e = cudaGetLastError()) {
+  static thread_local char buf[256];
+  snprintf(buf, sizeof(buf), "mps_gate2_update_noalloc: %s: %s", step, cudaGetErrorString(e));
+  return fail_msg(MPS_ERR_CUDA, buf);
 }
 
 struct Gate4 {
@@ -95,13 +103,13 @@ extern "C" int mps_gate2_update_noalloc(double* d_gamma_l, double* d_gamma_r, co
   if (!(cutoff >= 0.0)) return fail_msg(MPS_ERR_ARG, "cutoff must be >= 0");
   unsigned char* base = nullptr;
   const cudaError_t se = scratch_for_current_device(&base);
-  if (se != cudaSuccess) return fail_msg(MPS_ERR_CUDA, cudaGetErrorString(se));
+  if (se != cudaSuccess) return fail_cuda("looking up the scratch array", se);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // the bond dimensions live on the device: read the three ints (no allocation)
   int chi_h[3] = {0, 0, 0};
   if (cudaMemcpyAsync(chi_h, d_chi, sizeof(chi_h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
-    return fail_msg(MPS_ERR_CUDA, "reading the bond dimensions failed");
+    return fail_cuda("reading the bond dimensions");
   for (int i = 0; i < 3; ++i)
     if (chi_h[i] < 1 || chi_h[i] > chi_max) return fail_msg(MPS_ERR_ARG, "bond dimensions outside [1, chi_max]");
 
@@ -140,23 +148,26 @@ extern "C" int mps_gate2_update_noalloc(double* d_gamma_l, double* d_gamma_r, co
   launch_init_V(d_task, d_meta, 1, nw_ub, st);
   const int nb = (nw_ub + kBlockW - 1) / kBlockW;
   const int nbe = nb + (nb & 1);
-  for (int sw = 0; sw < 40; ++sw) {
+  for (int sw = 0; sw < kMaxSweeps; ++sw) {
     for (int r = 0; r < nbe - 1; ++r) launch_jacobi_round(d_task, d_meta, 1, r, nbe / 2, 0, nullptr, st);
-    if (cudaMemsetAsync(d_cnt, 0, sizeof(int), st) != cudaSuccess) return MPS_ERR_CUDA;
-    launch_sweep_end(d_meta, 1, 40, d_cnt, st);
+    if (cudaMemsetAsync(d_cnt, 0, sizeof(int), st) != cudaSuccess) return fail_cuda("clearing the sweep counter");
+    launch_sweep_end(d_meta, 1, kMaxSweeps, d_cnt, st);
     int active = 0;
-    if (cudaMemcpyAsync(&active, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return MPS_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return MPS_ERR_CUDA;
+    if (cudaMemcpyAsync(&active, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return fail_cuda("reading the sweep counter");
     if (active == 0) break;
   }
   launch_colnorms(d_task, d_meta, 1, nw_ub, 0, st);
   launch_truncate(d_task, d_meta, 1, 0, chi_max, st);
   launch_emit_left(d_task, d_meta, 1, chi_max, chi_max, 0, st);
   launch_emit_right(d_task, d_meta, 1, chi_max, chi_max, 0, st);
-  if (cudaGetLastError() != cudaSuccess) return MPS_ERR_CUDA;
+  const cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) return fail_cuda("a kernel launch", le);
   int status = 0;
-  if (cudaMemcpyAsync(&status, d_cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return MPS_ERR_CUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return MPS_ERR_CUDA;
+  if (cudaMemcpyAsync(&status, d_cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail_cuda("reading the status word");
   if (status != 0) return fail_msg(status, "Jacobi SVD did not converge (tensors left unchanged)");
   return MPS_OK;
 }

@@ -459,7 +459,7 @@ int ozaki_zgemm(const OzJob* d_jobs, int njobs, int M_ub, int N_ub, int K_ub, in
     cudaFree(buf.base);
     buf.base = nullptr;
     buf.bytes = 0;
-    if (cudaMalloc(&buf.base, need) != cudaSuccess) return -2;
+    if (dev_alloc((void**)&buf.base, need) != cudaSuccess) return -2;
     buf.bytes = need;
   }
   unsigned char* p = static_cast<unsigned char*>(buf.base);

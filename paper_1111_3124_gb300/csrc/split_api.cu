@@ -16,6 +16,9 @@ std::mutex g_mu;
 OzBuffers g_buf;
 OzJob* g_job = nullptr;
 int* g_err = nullptr;
+// Set once a bounded wait ran out: products may have been abandoned in flight,
+// so the device state is not trusted and later calls are refused.
+bool g_timed_out = false;
 
 int fail_msg(int code, const char* msg) {
   set_error_message(msg);
@@ -30,9 +33,10 @@ extern "C" int mps_split_zgemm(int M, int N, int K, const double* dA, long long 
   if (slices < 1 || slices > 8) return fail_msg(MPS_ERR_ARG, "slices must be 1..8");
   if (lda < M || ldb < K || ldc < M) return fail_msg(MPS_ERR_ARG, "leading dimension too small");
   std::lock_guard<std::mutex> lock(g_mu);
+  if (g_timed_out) return fail_msg(MPS_ERR_TIMEOUT, "an earlier split GEMM timed out; the device state is not trusted");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!g_job) {
-    if (cudaMalloc(&g_job, sizeof(OzJob)) != cudaSuccess || cudaMalloc(&g_err, sizeof(int)) != cudaSuccess)
+    if (dev_alloc((void**)&g_job, sizeof(OzJob)) != cudaSuccess || dev_alloc((void**)&g_err, sizeof(int)) != cudaSuccess)
       return fail_msg(MPS_ERR_NOMEM, "job table");
   }
   OzJob j = {};
@@ -58,6 +62,9 @@ extern "C" int mps_split_zgemm(int M, int N, int K, const double* dA, long long 
   if (cudaMemcpyAsync(&err, g_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return fail_msg(MPS_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
-  if (err) return fail_msg(MPS_ERR_TIMEOUT, "split GEMM: a bounded wait ran out");
+  if (err) {
+    g_timed_out = true;
+    return fail_msg(MPS_ERR_TIMEOUT, "split GEMM: a bounded wait ran out; the device state is not trusted");
+  }
   return MPS_OK;
 }

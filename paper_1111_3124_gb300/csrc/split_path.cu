@@ -319,10 +319,10 @@ __global__ void k_gram_x(const GateTask* tasks, TaskMeta* meta, int form_x) {
         }
         if (hypot(x.x, x.y) > kGramXMax) {
           // near-degenerate pair: left out of X and rotated exactly by
-          // k_givens (up to four per task, else the blocked sweeps)
+          // k_givens (up to kMaxGivens per task, else the blocked sweeps)
           if (ratio > tol && p < q) {
             const int slot = atomicAdd(&mt.nhard, 1);
-            if (slot < 4) {
+            if (slot < kMaxGivens) {
               const double t = hypot(x.x, x.y);
               const double sn = sin(t) / t;
               mt.hp[slot] = p;
@@ -408,7 +408,7 @@ __global__ void k_givens(const GateTask* tasks, const TaskMeta* meta) {
   const GateTask& tk = tasks[blockIdx.y];
   const TaskMeta& mt = meta[blockIdx.y];
   if (!polishing(mt) || mt.nhard <= 0) return;
-  const int nh = mt.nhard < 4 ? mt.nhard : 4;
+  const int nh = mt.nhard < kMaxGivens ? mt.nhard : kMaxGivens;
   const int rows = mt.Mw + mt.Nw;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
     double2* M = r < mt.Mw ? tk.A : tk.V;

@@ -871,10 +871,6 @@ void launch_sweep_end_nofail(TaskMeta* m, int ntask, int max_sweeps, int* active
   k_sweep_end<<<cdiv(ntask, 128), 128, 0, st>>>(m, ntask, max_sweeps, active_count, 0, 0.f);
 }
 
-void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub,
-                             unsigned long long* flops, cudaStream_t st) {
-  k_jacobi_pair<kBlockW32, float><<<dim3(pairs_ub, ntask), 256, 0, st>>>(t, m, round, 0, flops);
-}
 
 void launch_colnorms(const GateTask* t, const TaskMeta* m, int ntask, int nw_ub, int second, cudaStream_t st) {
   k_colnorms<<<dim3(cdiv(nw_ub, 8), ntask), 256, 0, st>>>(t, m, second);

@@ -68,6 +68,47 @@ def test_noalloc_matches_apply_gate_two_calls(torch_cuda):
         assert np.max(np.abs(mine - theirs)) < 1e-11 * np.max(np.abs(theirs))
 
 
+def test_noalloc_at_its_size_limit_matches_the_oracle(torch_cuda):
+    """chi_max = 64 with every touched bond saturated (theta 128 x 128, the
+    largest the fixed scratch array holds), two calls in a row, checked
+    against the CPU oracle and against mps_apply_gate."""
+    torch = torch_cuda
+    import oracle
+    from paper_1111_3124_gb300.mps import MPS, gate2_update_noalloc
+    cap, cutoff = 64, 1e-12
+    chi = (1, 64, 64, 64, 64, 1)
+    rng = np.random.default_rng(6464)
+    state = C.random_vidal_state(5, chi, rng, decay=2.0)
+    U1, U2 = C.haar_unitary(4, rng), C.haar_unitary(4, rng)
+    ref = MPS(5, cap, cutoff)
+    ref.import_state(*state)
+    orc = oracle.OracleMPS(5, cap, cutoff)
+    orc.set_state(*state)
+    gl, gr, ll, lm, lr, dchi = _device_tensors(torch, state, cap)
+    for U in (U1, U2):
+        ref.apply_gate(1, U)
+        orc.apply_gate(1, U)
+        gate2_update_noalloc(gl, gr, ll, lm, lr, dchi, cap, cutoff, U)
+        torch.cuda.synchronize()
+        k = int(dchi[1].item())
+        _, og, olam = orc.get_state()
+        assert k == len(olam[1]) == 64
+        _, rg, rlam = ref.export()
+        g_l = gl.cpu().numpy()[:, :64, :k]
+        g_r = gr.cpu().numpy()[:, :k, :64]
+        lam_m = lm.cpu().numpy()[:k]
+        assert spectrum_err(lam_m, olam[1]) < 1e-12
+        assert spectrum_err(lam_m, rlam[1]) < 1e-12
+        mine = two_site_tensor([og[0], g_l, g_r, og[3], og[4]], [olam[0], lam_m, olam[2], olam[3]], 1)
+        theirs = two_site_tensor(og, olam, 1)
+        assert np.max(np.abs(mine - theirs)) < 1e-11 * np.max(np.abs(theirs))
+        # continue both GPU paths from the oracle's state so the second call is teacher-forced
+        ref.import_state(og, olam)
+        st = _device_tensors(torch, (og, olam), cap)
+        for dst, src in zip((gl, gr, ll, lm, lr, dchi), st):
+            dst.copy_(src)
+
+
 def test_noalloc_rejects_oversized_chi_max(torch_cuda):
     torch = torch_cuda
     from paper_1111_3124_gb300.mps import MPSError, MPS_ERR_TOO_LARGE, gate2_update_noalloc
