@@ -4,11 +4,17 @@ Haar-random U(4) brickwork (+ RZ phases) workload at chi_max = 256.
 
 One step = the whole circuit from |0...0> (630 two-site updates: theta
 formation, Jacobi SVD, truncation, rewrite), inputs resident in HBM.
-Prints one JSON line (rank 0). See the design notes for the roofline
-definitions.
+Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
                   [--prec split|fp64] [--no-fp64-compare]
+  python bench.py --profile-layer [--n 64] [--chi 256] [--layers 1] [--prec split|fp64]
+
+--profile-layer runs the case that hardware-counter captures use: brickwork
+layers of Haar U(4) updates on a synthetic Vidal state with every bond at
+min(chi, 2^b, 2^(n-b)), so that every update works on a saturated 2chi x 2chi
+theta after only a few setup launches. It prints a one-line summary, not the
+bench line.
 
 The headline is the split-precision path (bf16-sliced tensor-core products,
 fp32 preconditioning sweeps, binary64 angles, tests and polish); the native
@@ -67,6 +73,9 @@ def args_parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--n", type=int, default=None, help="override the qubit count (small profiling cases)")
     p.add_argument("--depth", type=int, default=None, help="override the circuit depth")
+    p.add_argument("--profile-layer", action="store_true", help="run the saturated-layer capture case")
+    p.add_argument("--chi", type=int, default=256, help="bond dimension of the saturated-layer case")
+    p.add_argument("--layers", type=int, default=1, help="layers of the saturated-layer case")
     return p.parse_args()
 
 
@@ -387,8 +396,8 @@ def run_gpu(a):
     achieved = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else None
     name, bound, peak, src = roof_def[dom]
     # DRAM bytes per launch from one ncu capture of a saturated chi=256 layer
-    # (profiles/k_jacobi_pair_*_n64_chi256.md), scaled to this run's average
-    # launch by duration (both kernels are ALU-bound: time tracks work)
+    # (the --profile-layer case), scaled to this run's average launch by
+    # duration (both kernels are ALU-bound: time tracks work)
     captured = {0: (390.9e6, 2.2237), 4: (137.7e6, 0.2885)}  # class -> (bytes, ms) per launch
     ms_launch = d["ms"] / max(d["launches"], 1)
     traffic = captured[dom][0] * ms_launch / captured[dom][1] if dom in captured else None
@@ -435,10 +444,40 @@ def run_gpu(a):
         dist.destroy_process_group()
 
 
+def run_profile_layer(a):
+    """Brickwork layers on a synthetic saturated state (the capture case)."""
+    import torch
+    from paper_1111_3124_gb300 import build as B
+    from paper_1111_3124_gb300 import circuits as C
+    torch.cuda.set_device(0)
+    B.build()
+    from paper_1111_3124_gb300.mps import MPS, PREC_FP64, PREC_SPLIT
+    n = a.n or 64
+    rng = np.random.default_rng(C.SEED_BASE + 77)
+    chi = [1] + [min(a.chi, 2 ** min(b, n - b)) for b in range(1, n)] + [1]
+    gammas, lams = C.random_vidal_state(n, chi, rng, decay=2.0)
+    m = MPS(n, a.chi, 1e-12, PREC_SPLIT if a.prec == "split" else PREC_FP64)
+    m.import_state(gammas, lams)
+    nup = 0
+    t0 = time.perf_counter()
+    for layer in range(a.layers):
+        sites = C.brickwork_sites(n, layer)
+        Us = np.stack([C.haar_unitary(4, rng) for _ in sites])
+        m.apply_layer(sites, Us)
+        nup += len(sites)
+    m.sync()
+    dt = time.perf_counter() - t0
+    print("%d updates, %.3f s, max bond %d" % (nup, dt, int(m.bond_dims().max())))
+    m.close()
+
+
 def main():
     global ARGS
     a = args_parse()
     ARGS = a
+    if a.profile_layer:
+        run_profile_layer(a)
+        return
     if a.impl == "reference":
         import oracle
         oracle.build()

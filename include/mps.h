@@ -124,6 +124,20 @@ int mps_set_stream(mps_handle h, void* cuda_stream);
  * mps_svd_mode; MPS_SVD_SKETCH_MLP needs a predictor (mps_set_predictor). */
 int mps_set_mode(mps_handle h, int prec, int slices, int svd_mode);
 
+/* mps_set_limits - the sweep limit of the binary64 blocked Jacobi SVD of
+ * later gate updates (1 <= max_sweeps <= 60, default 60; the paper gives no
+ * limit, this engine's reading of Sec. 3.1's SVD). An update that reaches it
+ * without converging is left unapplied and reported as MPS_ERR_NOCONVERGE by
+ * the next synchronising call. Errors: MPS_ERR_ARG. */
+int mps_set_limits(mps_handle h, int max_sweeps);
+
+/* mps_debug_fail_alloc - test hook for the allocation-failure path (no paper
+ * counterpart): the next `after` device or pinned-host allocations made by
+ * the library succeed, the one after that is refused as if the device were out
+ * of memory (the call that needed it returns MPS_ERR_NOMEM and leaves the
+ * state as it was); after < 0 turns the hook off. Process-wide. */
+int mps_debug_fail_alloc(long long after);
+
 /* mps_reset - returns the state to |0...0> (same as a fresh mps_create). */
 int mps_reset(mps_handle h);
 
@@ -214,13 +228,20 @@ int mps_amplitudes(mps_handle h, int count, const unsigned char* bits, double* o
 int mps_expectation(mps_handle h, int site, int k, const double* O, double* out);
 
 /* mps_reduced_density - Sec. 3.2 ("RDO", the tracing-out operation): the
- * reduced density operator of the listed qubits, normalised to unit trace.
+ * reduced density operator of the listed qubits, normalised to unit trace,
+ * by a transfer-matrix contraction of Eq. (1) run from whichever end of the
+ * chain keeps the environments smaller.
  *   qubits  host array of nq distinct qubit indices in any order; the first
  *           listed qubit is the most significant bit of rho's index (as in
  *           the Sec. 3.2 output |00><11|)
- *   nq      1 <= nq <= 6
+ *   nq      1 <= nq <= 12
  *   rho     host buffer of 2^nq x 2^nq complex128, row-major
- * Errors: MPS_ERR_ARG, MPS_ERR_TOO_LARGE (nq > 6). Synchronises the stream. */
+ * The contraction holds 4^t x chi^2 entries after t listed qubits (chi the
+ * bond it has reached); a request that would hold more than 2^27 entries in
+ * one buffer is refused with MPS_ERR_TOO_LARGE. The working buffers are the
+ * handle's (grown on demand, released by mps_destroy).
+ * Errors: MPS_ERR_ARG, MPS_ERR_TOO_LARGE (nq > 12 or the size above),
+ * MPS_ERR_NOMEM. Synchronises the stream. */
 int mps_reduced_density(mps_handle h, const int* qubits, int nq, double* rho);
 
 /* mps_get_schmidt - copies Lambda_bond (the Schmidt coefficients of the cut

@@ -144,6 +144,9 @@ struct mps_state {
   // products may have been abandoned in flight, so the handle's device state is
   // no longer trusted and every later split-precision product is refused.
   int oz_timed_out = 0;
+  // readout workspace (reduced densities, expectations)
+  double2* ro_buf = nullptr;
+  size_t ro_bytes = 0;
 };
 
 namespace {
@@ -297,6 +300,7 @@ void free_state(mps_state* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   cudaFree(h->arena);
   cudaFree(h->sk_arena);
+  cudaFree(h->ro_buf);
   cudaFree(h->d_oz_jobs); cudaFree(h->d_oz_err); cudaFree(h->oz_buf.base);
   cudaFree(h->gamma); cudaFree(h->lambda); cudaFree(h->chi);
   cudaFree(h->d_tasks); cudaFree(h->d_meta); cudaFree(h->d_gates); cudaFree(h->d_counter);
@@ -1282,7 +1286,28 @@ int read_chi(mps_state* h, std::vector<int>& chi) {
   return MPS_OK;
 }
 
-// Reduced density operator of `qubits` by transfer-matrix contraction.
+// Readout workspace of the handle (grown on demand, kept until destroy).
+int ensure_readout(mps_state* h, size_t elems) {
+  const size_t bytes = elems * sizeof(double2);
+  if (bytes <= h->ro_bytes) return MPS_OK;
+  CK(cudaStreamSynchronize(h->stream));
+  cudaFree(h->ro_buf);
+  h->ro_buf = nullptr;
+  h->ro_bytes = 0;
+  CK(dev_alloc((void**)&h->ro_buf, bytes));
+  h->ro_bytes = bytes;
+  return MPS_OK;
+}
+
+// Largest working set of a reduced-density contraction (complex entries per
+// environment buffer) and of its partial products.
+constexpr size_t kRdoBudget = (size_t)1 << 27;
+
+// Reduced density operator of `qubits` by transfer-matrix contraction of
+// Eq. (1) (the tracing-out of Sec. 3.2). The environment runs from the end of
+// the chain nearer to the listed qubits' far side (left to right or right to
+// left, whichever holds fewer entries), opening a (ket, bra) index pair at
+// every listed qubit: environments are blocks indexed by the open pairs so far.
 int rdo_impl(mps_state* h, const int* qubits, int nq, std::vector<cd>& rho) {
   std::vector<int> pos(h->n, -1);
   for (int t = 0; t < nq; ++t) pos[qubits[t]] = t;
@@ -1291,51 +1316,80 @@ int rdo_impl(mps_state* h, const int* qubits, int nq, std::vector<cd>& rho) {
   std::vector<int> chi;
   rc = read_chi(h, chi);
   if (rc) return rc;
-  // buffer sizes: blocks * dim^2 for E, blocks * xl * xr for tmp (x2 for open sites)
-  size_t e_max = 1, t_max = 1, s_max = 1;
-  {
+  // working sets of both directions: environments (nblk * bond^2), partial
+  // products (2 nblk xl xr), the scaled site (2 xl xr)
+  auto sizes = [&](bool l2r, size_t& e_max, size_t& t_max, size_t& s_max) {
+    e_max = t_max = s_max = 1;
     size_t nblk = 1;
-    for (int s = 0; s < h->n; ++s) {
+    for (int k = 0; k < h->n; ++k) {
+      const int s = l2r ? k : h->n - 1 - k;
       const size_t xl = chi[s], xr = chi[s + 1];
-      const size_t tb = (pos[s] >= 0 ? 2 : 1) * nblk * xl * xr;
+      const size_t in_b = l2r ? xl : xr, out_b = l2r ? xr : xl;
+      t_max = std::max(t_max, (pos[s] >= 0 ? 2 : 1) * nblk * xl * xr);
       if (pos[s] >= 0) nblk *= 4;
-      e_max = std::max(e_max, std::max(nblk * xr * xr, nblk * xl * xl));
-      t_max = std::max(t_max, tb);
+      e_max = std::max(e_max, std::max(nblk * out_b * out_b, nblk * in_b * in_b));
       s_max = std::max(s_max, 2 * xl * xr);
     }
-  }
-  if (e_max > (size_t)1 << 27 || t_max > (size_t)1 << 27) return fail(MPS_ERR_TOO_LARGE, "reduced density too large");
-  double2 *E0 = nullptr, *E1 = nullptr, *Tm = nullptr, *Sc = nullptr;
-  auto cleanup = [&]() { cudaFree(E0); cudaFree(E1); cudaFree(Tm); cudaFree(Sc); };
-  if (dev_alloc((void**)&E0, e_max * sizeof(double2)) != cudaSuccess || dev_alloc((void**)&E1, e_max * sizeof(double2)) != cudaSuccess ||
-      dev_alloc((void**)&Tm, t_max * sizeof(double2)) != cudaSuccess || dev_alloc((void**)&Sc, s_max * sizeof(double2)) != cudaSuccess) {
-    cleanup();
-    return fail(MPS_ERR_NOMEM, "reduced density buffers");
-  }
+  };
+  size_t e_l, t_l, s_l, e_r, t_r, s_r;
+  sizes(true, e_l, t_l, s_l);
+  sizes(false, e_r, t_r, s_r);
+  const bool l2r = std::max(e_l, t_l) <= std::max(e_r, t_r);
+  const size_t e_max = l2r ? e_l : e_r, t_max = l2r ? t_l : t_r, s_max = l2r ? s_l : s_r;
+  if (e_max > kRdoBudget || t_max > kRdoBudget)
+    return fail(MPS_ERR_TOO_LARGE, "reduced density: the contraction would hold more than 2^27 entries per buffer");
+  if ((rc = ensure_readout(h, 2 * e_max + t_max + s_max))) return rc;
+  double2* E0 = h->ro_buf;
+  double2* E1 = E0 + e_max;
+  double2* Tm = E1 + e_max;
+  double2* Sc = Tm + t_max;
   const double2 one = make_double2(1.0, 0.0);
-  cudaMemcpyAsync(E0, &one, sizeof(double2), cudaMemcpyHostToDevice, h->stream);
-  int nblk = 1;
-  for (int s = 0; s < h->n; ++s) {
+  CK(cudaMemcpyAsync(E0, &one, sizeof(double2), cudaMemcpyHostToDevice, h->stream));
+  long long nblk = 1;
+  std::vector<int> open;  // open sites in traversal order: block digit t (base 4, least significant first)
+  for (int k = 0; k < h->n; ++k) {
+    const int s = l2r ? k : h->n - 1 - k;
     const int xl = chi[s], xr = chi[s + 1];
     launch_scale_site(site_ptr(h, s), bond_ptr(h, s), xl, xr, h->cap, Sc, h->stream);
-    const long long sE = (long long)xl * xl, sT = (long long)xr * xl, sN = (long long)xr * xr;
-    if (pos[s] < 0) {
-      for (int i = 0; i < 2; ++i) {
-        const double2* Ai = Sc + (size_t)i * xl * xr;
-        // tmp_b = A_i^T E_b  (xr x xl)
-        launch_zgemm(xr, xl, xl, Ai, xr, 0, 1, E0, xl, sE, 0, Tm, xl, sT, 0, nblk, h->stream);
-        // E'_b (+)= tmp_b conj(A_i)  (xr x xr)
-        launch_zgemm(xr, xr, xl, Tm, xl, sT, 0, Ai, xr, 0, 1, E1, xr, sN, i, nblk, h->stream);
+    const double2* A[2] = {Sc, Sc + (size_t)xl * xr};  // A_i[a][c] = Gamma_s[i][a][c] Lambda_s[c]
+    if (l2r) {
+      // E'[c][c'] = sum_{a a'} A_i[a][c] E[a][a'] conj(A_j[a'][c'])
+      const long long sE = (long long)xl * xl, sT = (long long)xr * xl, sN = (long long)xr * xr;
+      if (pos[s] < 0) {
+        for (int i = 0; i < 2; ++i) {
+          launch_zgemm(xr, xl, xl, A[i], xr, 0, 1, E0, xl, sE, 0, 0, Tm, xl, sT, 0, nblk, h->stream);
+          launch_zgemm(xr, xr, xl, Tm, xl, sT, 0, A[i], xr, 0, 1, 0, E1, xr, sN, i, nblk, h->stream);
+        }
+      } else {
+        for (int i = 0; i < 2; ++i)
+          launch_zgemm(xr, xl, xl, A[i], xr, 0, 1, E0, xl, sE, 0, 0, Tm + (size_t)i * nblk * sT, xl, sT, 0, nblk,
+                       h->stream);
+        for (int i = 0; i < 2; ++i)
+          for (int j = 0; j < 2; ++j)
+            launch_zgemm(xr, xr, xl, Tm + (size_t)i * nblk * sT, xl, sT, 0, A[j], xr, 0, 1, 0,
+                         E1 + (size_t)(i * 2 + j) * nblk * sN, xr, sN, 0, nblk, h->stream);
       }
     } else {
-      for (int i = 0; i < 2; ++i)
-        launch_zgemm(xr, xl, xl, Sc + (size_t)i * xl * xr, xr, 0, 1, E0, xl, sE, 0, Tm + (size_t)i * nblk * sT, xl,
-                     sT, 0, nblk, h->stream);
-      for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 2; ++j)
-          launch_zgemm(xr, xr, xl, Tm + (size_t)i * nblk * sT, xl, sT, 0, Sc + (size_t)j * xl * xr, xr, 0, 1,
-                       E1 + (size_t)(i * 2 + j) * nblk * sN, xr, sN, 0, nblk, h->stream);
+      // F'[a][a'] = sum_{c c'} A_i[a][c] F[c][c'] conj(A_j[a'][c'])
+      const long long sF = (long long)xr * xr, sT = (long long)xl * xr, sN = (long long)xl * xl;
+      if (pos[s] < 0) {
+        for (int i = 0; i < 2; ++i) {
+          launch_zgemm(xl, xr, xr, A[i], xr, 0, 0, E0, xr, sF, 0, 0, Tm, xr, sT, 0, nblk, h->stream);
+          launch_zgemm(xl, xl, xr, Tm, xr, sT, 0, A[i], xr, 0, 1, 1, E1, xl, sN, i, nblk, h->stream);
+        }
+      } else {
+        for (int i = 0; i < 2; ++i)
+          launch_zgemm(xl, xr, xr, A[i], xr, 0, 0, E0, xr, sF, 0, 0, Tm + (size_t)i * nblk * sT, xr, sT, 0, nblk,
+                       h->stream);
+        for (int i = 0; i < 2; ++i)
+          for (int j = 0; j < 2; ++j)
+            launch_zgemm(xl, xl, xr, Tm + (size_t)i * nblk * sT, xr, sT, 0, A[j], xr, 0, 1, 1,
+                         E1 + (size_t)(i * 2 + j) * nblk * sN, xl, sN, 0, nblk, h->stream);
+      }
+    }
+    if (pos[s] >= 0) {
       nblk *= 4;
+      open.push_back(s);
     }
     std::swap(E0, E1);
   }
@@ -1343,20 +1397,15 @@ int rdo_impl(mps_state* h, const int* qubits, int nq, std::vector<cd>& rho) {
   cudaError_t ce = cudaMemcpyAsync(vals.data(), E0, sizeof(double2) * nblk, cudaMemcpyDeviceToHost, h->stream);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
   if (ce == cudaSuccess) ce = cudaGetLastError();
-  cleanup();
   if (ce != cudaSuccess) return fail(MPS_ERR_CUDA, std::string("reduced density: ") + cudaGetErrorString(ce));
-  // open sites in site order; block index = sum_t (i_t*2 + j_t) 4^(t-1), t = 1..m
-  std::vector<int> open;
-  for (int s = 0; s < h->n; ++s)
-    if (pos[s] >= 0) open.push_back(s);
   const int dim = 1 << nq;
   rho.assign((size_t)dim * dim, cd(0));
   cd tr = 0;
-  for (int blk = 0; blk < nblk; ++blk) {
+  for (long long blk = 0; blk < nblk; ++blk) {
     int x = 0, y = 0;
     bool diag = true;
     for (int t = 0; t < nq; ++t) {
-      const int pr = (blk >> (2 * t)) & 3, i = pr >> 1, j = pr & 1;
+      const int pr = (int)((blk >> (2 * t)) & 3), i = pr >> 1, j = pr & 1;
       const int sh = nq - 1 - pos[open[t]];
       x |= i << sh;
       y |= j << sh;
@@ -1590,7 +1639,7 @@ int mps_amplitude(mps_handle h, const unsigned char* bits, double* out) { return
 int mps_reduced_density(mps_handle h, const int* qubits, int nq, double* rho) {
   if (!h || !qubits || !rho) return fail(MPS_ERR_ARG, "bad arguments");
   if (nq < 1) return fail(MPS_ERR_ARG, "nq must be >= 1");
-  if (nq > 6) return fail(MPS_ERR_TOO_LARGE, "nq > 6");
+  if (nq > 12) return fail(MPS_ERR_TOO_LARGE, "nq > 12");
   std::vector<char> seen(h->n, 0);
   for (int t = 0; t < nq; ++t) {
     if (qubits[t] < 0 || qubits[t] >= h->n || seen[qubits[t]]) return fail(MPS_ERR_ARG, "bad qubit list");

@@ -319,7 +319,8 @@ __global__ void __launch_bounds__(256, 3)
   const int bi = tid / NP, bj = tid % NP;  // row pair, column pair of this thread's 2 x 2 block
   const int lane = tid & 31;
   const bool blk_warp = (tid & ~31) < NP * NP;  // warps holding 2 x 2 blocks (NP * NP is a multiple of 32)
-  for (int ir = 0; ir < C2 - 1; ++ir) {
+  for (int it = 0; it < kF32InnerSweeps * (C2 - 1); ++it) {
+    const int ir = it % (C2 - 1);
     Rot ri = {1.f, zero, 0.f, false}, rj = ri;
     int Pi = 0, Qi = 0, Pj = 0, Qj = 0;
     float2 x00 = zero, x01 = zero, x10 = zero, x11 = zero;

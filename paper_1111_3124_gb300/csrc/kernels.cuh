@@ -6,6 +6,7 @@ namespace mpsgb {
 
 constexpr int kBlockW = 8;     // Jacobi block width b (columns per block), binary64 sweeps
 constexpr int kBlockW32 = 16;  // block width of the fp32 preconditioning sweeps
+constexpr int kF32InnerSweeps = 1;  // inner Hermitian Jacobi sweeps per block pair in the fp32 sweeps
 constexpr float kQuadStop = 1e-8f;  // binary64 sweeps stop after one whose max scaled off-diagonal < this
 constexpr int kInnerSweepsFar = 1;  // inner sweeps of a block pair whose off-diagonal is above kQuadStop ...
 constexpr int kInnerFarSweeps = 30;  // ... during a task's first sweeps
@@ -46,7 +47,7 @@ void launch_amplitudes(const double2* gamma, const double* lambda, const int* ch
                        const unsigned char* bits, int count, double2* out, cudaStream_t st);
 void launch_scale_site(const double2* g, const double* lam, int xl, int xr, int cap, double2* out, cudaStream_t st);
 void launch_zgemm(int M, int N, int K, const double2* A, int lda, long long sA, int transA, const double2* B,
-                  int ldb, long long sB, int conjB, double2* C, int ldc, long long sC, int accumulate, int batch,
-                  cudaStream_t st);
+                  int ldb, long long sB, int conjB, int transB, double2* C, int ldc, long long sC, int accumulate,
+                  long long batch, cudaStream_t st);
 
 }  // namespace mpsgb

@@ -51,10 +51,11 @@ __global__ void k_scale_site(const double2* g, const double* lam, int xl, int xr
   }
 }
 
-// C_z (+)= op(A_z) op(B_z), 16x16 tiles. opA: A^T if transA; opB: conj(B) if conjB.
+// C_z (+)= op(A_z) op(B_z), 16x16 tiles, row-major operands. opA: A^T if
+// transA; opB: B^T if transB, then conjugated if conjB.
 __global__ void __launch_bounds__(256) k_zgemm(int M, int N, int K, const double2* A, int lda, long long sA,
                                                int transA, const double2* B, int ldb, long long sB, int conjB,
-                                               double2* C, int ldc, long long sC, int accumulate) {
+                                               int transB, double2* C, int ldc, long long sC, int accumulate) {
   __shared__ double2 As[16][17], Bs[16][17];
   A += sA * blockIdx.z;
   B += sB * blockIdx.z;
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(256) k_zgemm(int M, int N, int K, const double
       const int kk = k0 + ty;
       double2 v = make_double2(0.0, 0.0);
       if (kk < K && n < N) {
-        v = B[(size_t)kk * ldb + n];
+        v = transB ? B[(size_t)n * ldb + kk] : B[(size_t)kk * ldb + n];
         if (conjB) v.y = -v.y;
       }
       Bs[ty][tx] = v;
@@ -107,10 +108,15 @@ void launch_scale_site(const double2* g, const double* lam, int xl, int xr, int 
 }
 
 void launch_zgemm(int M, int N, int K, const double2* A, int lda, long long sA, int transA, const double2* B,
-                  int ldb, long long sB, int conjB, double2* C, int ldc, long long sC, int accumulate, int batch,
-                  cudaStream_t st) {
-  dim3 g((N + 15) / 16, (M + 15) / 16, batch);
-  k_zgemm<<<g, 256, 0, st>>>(M, N, K, A, lda, sA, transA, B, ldb, sB, conjB, C, ldc, sC, accumulate);
+                  int ldb, long long sB, int conjB, int transB, double2* C, int ldc, long long sC, int accumulate,
+                  long long batch, cudaStream_t st) {
+  // the batch runs in grid.z chunks of at most 65535
+  for (long long b0 = 0; b0 < batch; b0 += 65535) {
+    const int nb = (int)(batch - b0 < 65535 ? batch - b0 : 65535);
+    dim3 g((N + 15) / 16, (M + 15) / 16, nb);
+    k_zgemm<<<g, 256, 0, st>>>(M, N, K, A + sA * b0, lda, sA, transA, B + sB * b0, ldb, sB, conjB, transB,
+                               C + sC * b0, ldc, sC, accumulate);
+  }
 }
 
 }  // namespace mpsgb

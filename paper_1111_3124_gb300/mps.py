@@ -35,7 +35,7 @@ EXPORTS = [
     "mps_get_schmidt", "mps_bond_dims", "mps_export", "mps_import", "mps_diag", "mps_sync", "mps_last_error",
     "mps_gate2_update_noalloc", "mps_split_zgemm", "mps_apply_layer_multi",
     "mps_mlp_create", "mps_mlp_destroy", "mps_mlp_params", "mps_mlp_forward", "mps_mlp_loss_grad", "mps_mlp_train",
-    "mps_layer_features", "mps_set_predictor", "mps_sketch_stats",
+    "mps_layer_features", "mps_set_predictor", "mps_sketch_stats", "mps_set_limits", "mps_debug_fail_alloc",
 ]
 
 
@@ -95,6 +95,8 @@ def load_library(path: str = LIB_PATH):
         "mps_set_predictor": [P, P],
         "mps_sketch_stats": [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_longlong)],
+        "mps_set_limits": [P, I],
+        "mps_debug_fail_alloc": [ctypes.c_longlong],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -155,6 +157,9 @@ class MPS:
 
     def reset(self) -> None:
         check(load_library().mps_reset(self._h))
+
+    def set_limits(self, max_sweeps: int) -> None:
+        check(load_library().mps_set_limits(self._h, max_sweeps))
 
     def apply_gate(self, site: int, U) -> None:
         U = _c128(U)
@@ -312,6 +317,11 @@ class MPS:
                 if d >= 4:
                     nup += len(gs)
         return nup
+
+
+def debug_fail_alloc(after: int) -> None:
+    """Test hook: the allocation after the next `after` ones fails (-1: off)."""
+    check(load_library().mps_debug_fail_alloc(int(after)))
 
 
 def gate2_update_noalloc(gamma_l, gamma_r, lambda_l, lambda_m, lambda_r, chi, chi_max: int, cutoff: float, U,
