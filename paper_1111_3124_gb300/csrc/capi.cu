@@ -51,6 +51,7 @@ constexpr int kProfKinds = 6;  // see mps_profile in include/mps.h
 constexpr int kSplitMaxCap = kMaxCap;  // the split GEMM chunks K beyond 512
 constexpr int kF32Sweeps = 30;
 constexpr int kGramSteps = 3;  // simultaneous-rotation steps of the split path's Gram polish
+constexpr int kRotTcMinNw = 64;  // smallest working-matrix width whose fp32 rotations use the tensor cores
 
 // Memory budget of one batched pass: the tasks of a layer (or of many
 // circuits' layers) are processed in chunks whose workspace fits this.
@@ -97,6 +98,7 @@ struct mps_state {
   double cutoff = 0.0;
   int prec = MPS_PREC_FP64, slices = 8, svd_mode = 0;
   int max_sweeps = kMaxSweeps;  // binary64 Jacobi sweep limit (mps_set_limits)
+  int rot_tc = 0;               // fp32 sweeps rotate on the tensor cores (k_rot_tc) instead of in the pair kernel
   cudaStream_t own = nullptr, stream = nullptr;
   double2* gamma = nullptr;
   double* lambda = nullptr;
@@ -226,7 +228,7 @@ struct TaskRef {
 // A (Mw x Nw), V (Nw x Nw, both splits of a three-site gate), T, sigma/perm,
 // and for the split-precision path A32, V32, P, Q, V2.
 struct TaskLayout {
-  size_t off[10];
+  size_t off[12];
   size_t total;
 };
 
@@ -235,7 +237,7 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 TaskLayout task_layout(const TaskRef& r, int k, bool split) {
   const mps_state* st = r.st;
   const size_t xl = st->ub[r.site], xr = st->ub[r.site + k], cap = st->cap;
-  size_t sz[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  size_t sz[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (k == 3) {
     const size_t m1 = 2 * xl, n1 = 4 * xr;
     const size_t nw1 = std::min(m1, n1), mw1 = std::max(m1, n1);
@@ -268,9 +270,21 @@ TaskLayout task_layout(const TaskRef& r, int k, bool split) {
       sz[7] = sz[8] = sz[9] = nw * nw * sizeof(double2);
     }
   }
+  if (split) {  // the fp32 sweeps' per-block-pair rotations (b = 16)
+    size_t nw = 1;
+    if (k == 3) {
+      const size_t m1 = 2 * xl, n1 = 4 * xr, k1 = std::min(cap, std::min(m1, n1));
+      nw = std::max(std::min(m1, n1), std::min(2 * k1, 2 * xr));
+    } else {
+      nw = std::min(2 * xl, 2 * xr);
+    }
+    const size_t pairs = (nw + 31) / 32 + 1;
+    sz[10] = pairs * 32 * 32 * sizeof(float2);
+    sz[11] = pairs * sizeof(int);
+  }
   TaskLayout L;
   size_t o = 0;
-  for (int i = 0; i < 10; ++i) {
+  for (int i = 0; i < 12; ++i) {
     L.off[i] = o;
     o += align256(sz[i]);
   }
@@ -474,15 +488,18 @@ int oz_gemm(mps_state* h, int ng, int kind, int M_ub, int N_ub, int K_ub, int sl
 
 // fp32 preconditioning sweeps on (A32, V32) of every task, then re-arm the
 // tasks (the binary64 sweeps reuse the active/sweep counters).
-int run_f32_sweeps(mps_state* h, int ng, int nw_ub) {
+int run_f32_sweeps(mps_state* h, int ng, int mw_ub, int nw_ub) {
   const int nb = (nw_ub + kBlockW32 - 1) / kBlockW32;
   const int nbe = nb + (nb & 1);
   unsigned long long* fl = h->prof ? h->d_prof_flops + 4 : nullptr;
+  // block rotations on the tensor cores once a pair's rows fill MMA tiles
+  const bool tc = h->rot_tc && nw_ub >= kRotTcMinNw;
   for (int sw = 0; sw < kF32Sweeps; ++sw) {
     for (int r = 0; r < nbe - 1; ++r) {
       const int ev = pbeg(h);
-      launch_jacobi_round_f32(h->d_tasks, h->d_meta, ng, r, nbe / 2, kBlockW32, fl, h->stream);
-      pend(h, 4, ev, 1);
+      launch_jacobi_round_f32(h->d_tasks, h->d_meta, ng, r, nbe / 2, kBlockW32, tc ? 0 : 1, fl, h->stream);
+      if (tc) launch_rot_tc(h->d_tasks, h->d_meta, ng, r, nbe / 2, mw_ub, nw_ub, h->d_oz_err, h->stream);
+      pend(h, 4, ev, tc ? 2 : 1);
     }
     CK(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
     launch_sweep_end_nofail(h->d_meta, ng, kF32Sweeps, h->d_counter, h->stream);
@@ -504,7 +521,9 @@ int run_split_svd(mps_state* h, int ng, int mw_ub, int nw_ub) {
   int ev = pbeg(h);
   launch_to_f32(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub + (long long)nw_ub * nw_ub, h->stream);
   pend(h, 5, ev, 1);
-  int rc = run_f32_sweeps(h, ng, nw_ub);
+  int rc = ensure_oz(h, ng);  // its error word also serves the tensor-core rotation
+  if (rc) return rc;
+  rc = run_f32_sweeps(h, ng, mw_ub, nw_ub);
   if (rc) return rc;
   ev = pbeg(h);
   launch_v_to_f64(h->d_tasks, h->d_meta, ng, (long long)nw_ub * nw_ub, h->stream);
@@ -635,6 +654,8 @@ int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const
     t.P = reinterpret_cast<double2*>(tb + o[7]);
     t.Q = reinterpret_cast<double2*>(tb + o[8]);
     t.V2 = reinterpret_cast<double2*>(tb + o[9]);
+    t.Wp = reinterpret_cast<float2*>(tb + o[10]);
+    t.Wneed = reinterpret_cast<int*>(tb + o[11]);
     w->h_tasks[g] = t;
     const int xl = h->ub[s], x0 = h->ub[s + 1], xr = h->ub[s + k];
     xl_ub = std::max(xl_ub, xl);

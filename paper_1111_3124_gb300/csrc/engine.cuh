@@ -47,6 +47,8 @@ struct GateTask {
   double2* P;           // Nw x Nw scratch: V^H V; the Gram polish's G, X, W
   double2* Q;           // Nw x Nw scratch: V P; X^2; V W
   double2* V2;          // Nw x Nw scratch: X^3, then the column scales of A W
+  float2* Wp;           // fp32 sweeps: each block pair's 32 x 32 rotation W (for the tensor-core rotation)
+  int* Wneed;           //   and whether that pair rotated in this round
 };
 
 // Per-task state written and read by kernels only.

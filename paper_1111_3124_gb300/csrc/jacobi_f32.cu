@@ -137,7 +137,10 @@ struct JacobiSmem {
 
 }  // namespace
 
-template <int BW>
+// FUSED: the CTA rotates the columns of A32 and V32 itself (step 4 below).
+// Otherwise it writes W (and whether the pair rotated) to the task's Wp /
+// Wneed, and k_rot_tc applies W on the tensor cores.
+template <int BW, bool FUSED>
 __global__ void __launch_bounds__(256, 3)
     k_jacobi_pair_f32(const GateTask* tasks, TaskMeta* meta, int round, unsigned long long* flops) {
   constexpr int C2 = 2 * BW;                // columns of a block pair
@@ -311,7 +314,10 @@ __global__ void __launch_bounds__(256, 3)
   int nv = 0;
   for (int c = 0; c < C2; ++c) nv += cols[c] >= 0;
   if (!need) {
-    if (flops && tid == 0) atomicAdd(flops, 4ull * nv * (nv + 1) * (unsigned long long)Mw);
+    if (tid == 0) {
+      if (flops) atomicAdd(flops, 4ull * nv * (nv + 1) * (unsigned long long)Mw);
+      if (!FUSED) tk.Wneed[blockIdx.x] = 0;
+    }
     return;
   }
 
@@ -384,6 +390,19 @@ __global__ void __launch_bounds__(256, 3)
     __syncthreads();
   }
 
+  if (!FUSED) {  // hand W to the tensor-core rotation
+    float2* Wo = tk.Wp + (size_t)blockIdx.x * C2 * C2;
+    for (int e = tid; e < C2 * C2; e += 256) Wo[e] = W[e / C2][e % C2];
+    if (tid == 0) {
+      tk.Wneed[blockIdx.x] = 1;
+      mt.rotated = 1;
+      if (flops)
+        atomicAdd(flops, 4ull * nv * (nv + 1) * (unsigned long long)Mw + 60ull * C2 * (unsigned long long)nrot +
+                             8ull * nv * C2 * (unsigned long long)(Mw + Nw));
+    }
+    return;
+  }
+
   // ---- 4. [A_I A_J] W and [V_I V_J] W
   const int slot = tid % SLOTS, cg = tid / SLOTS;
   const int nch_v = (Nw + RCH - 1) / RCH;
@@ -440,24 +459,26 @@ __global__ void __launch_bounds__(256, 3)
   }
 }
 
-template <int BW>
+template <int BW, bool FUSED>
 static void launch_pair_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub,
                             unsigned long long* flops, cudaStream_t st) {
   static bool attr = false;
   constexpr int bytes = (int)sizeof(JacobiSmem<BW>);
   if (!attr) {
-    cudaFuncSetAttribute(k_jacobi_pair_f32<BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_jacobi_pair_f32<BW, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     attr = true;
   }
-  k_jacobi_pair_f32<BW><<<dim3(pairs_ub, ntask), 256, bytes, st>>>(t, m, round, flops);
+  k_jacobi_pair_f32<BW, FUSED><<<dim3(pairs_ub, ntask), 256, bytes, st>>>(t, m, round, flops);
 }
 
-void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub, int bw,
+void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub, int bw, int fused,
                              unsigned long long* flops, cudaStream_t st) {
   if (bw == 8)
-    launch_pair_f32<8>(t, m, ntask, round, pairs_ub, flops, st);
+    launch_pair_f32<8, true>(t, m, ntask, round, pairs_ub, flops, st);
+  else if (fused)
+    launch_pair_f32<16, true>(t, m, ntask, round, pairs_ub, flops, st);
   else
-    launch_pair_f32<16>(t, m, ntask, round, pairs_ub, flops, st);
+    launch_pair_f32<16, false>(t, m, ntask, round, pairs_ub, flops, st);
 }
 
 }  // namespace mpsgb

@@ -31,9 +31,13 @@ void launch_jacobi_round(const GateTask* t, TaskMeta* m, int ntask, int round, i
                          unsigned long long* flops, cudaStream_t st);
 void launch_sweep_end(TaskMeta* m, int ntask, int max_sweeps, int* active_count, cudaStream_t st);
 void launch_sweep_end_nofail(TaskMeta* m, int ntask, int max_sweeps, int* active_count, cudaStream_t st);
-// fp32 preconditioning round (jacobi_f32.cu), block width bw = 8 or 16.
-void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub, int bw,
+// fp32 preconditioning round (jacobi_f32.cu), block width bw = 8 or 16. With
+// fused = 0 (bw = 16 only) the pair kernel writes W and launch_rot_tc
+// (jacobi_rot_tc.cu) applies it to the rows of A32 and V32 on the tensor cores.
+void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub, int bw, int fused,
                              unsigned long long* flops, cudaStream_t st);
+void launch_rot_tc(const GateTask* t, const TaskMeta* m, int ntask, int round, int pairs_ub, int mw_ub, int nw_ub,
+                   int* err, cudaStream_t st);
 void launch_colnorms(const GateTask* t, const TaskMeta* m, int ntask, int nw_ub, int second, cudaStream_t st);
 void launch_truncate(const GateTask* t, TaskMeta* m, int ntask, int stage, int chi_cap, cudaStream_t st);
 void launch_emit_left(const GateTask* t, const TaskMeta* m, int ntask, int r_ub, int k_ub, int stage,
