@@ -74,6 +74,11 @@ def args_parse():
     p.add_argument("--n", type=int, default=None, help="override the qubit count (small profiling cases)")
     p.add_argument("--depth", type=int, default=None, help="override the circuit depth")
     p.add_argument("--profile-layer", action="store_true", help="run the saturated-layer capture case")
+    p.add_argument("--path", default="program", choices=["program", "eager"],
+                   help="timed path: the circuit recorded once and replayed as a CUDA graph, or host-driven passes")
+    p.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the binary64 comparison")
+    p.add_argument("--no-extra-configs", action="store_true", help="skip the three-site and many-circuit lines")
+    p.add_argument("--batch-circuits", type=int, default=32, help="circuits of the many-circuit line")
     p.add_argument("--chi", type=int, default=256, help="bond dimension of the saturated-layer case")
     p.add_argument("--layers", type=int, default=1, help="layers of the saturated-layer case")
     return p.parse_args()
@@ -264,6 +269,117 @@ def job_throughput(units_per_rank: float, world: int, seconds: float) -> float:
 
 # ------------------------------------------------------------- GPU arm ---
 
+def program_passes(dev_layers):
+    """The circuit's device layers as recorded-program passes (one handle)."""
+    return [(k, [(0, int(q)) for q in s], dU) for k, s, dU in dev_layers]
+
+
+def oracle_check(prec, n_updates: int):
+    """The saturated chi = 256 update of the CPU-baseline sample (synthetic
+    saturated state, Haar U(4), theta 512 x 512 cut to 256) on the GPU, against
+    the oracle: largest Schmidt-value error relative to lambda_0 and largest
+    error of the reconstructed two-site tensor relative to its largest entry."""
+    import oracle
+    from paper_1111_3124_gb300 import circuits as C
+    from paper_1111_3124_gb300.mps import MPS
+    spec, theta = 0.0, 0.0
+    for i in range(n_updates):
+        rng = np.random.default_rng(9000 + i)
+        state = C.random_vidal_state(4, (1, 256, 256, 256, 1), rng, decay=2.0)
+        U = C.haar_unitary(4, rng)
+        orc = oracle.OracleMPS(4, 256, 1e-12)
+        orc.set_state(*state)
+        orc.apply_gate(1, U)
+        g = MPS(4, 256, 1e-12, prec)
+        g.import_state(*state)
+        g.apply_gate(1, U)
+        _, og, ol = orc.get_state()
+        _, gg, gl = g.export()
+        g.close()
+        if len(ol[1]) != len(gl[1]):
+            return {"max_spectrum_err": float("inf"), "max_theta_err": float("inf"), "updates": n_updates}
+        spec = max(spec, float(np.max(np.abs(ol[1] - gl[1])) / ol[1][0]))
+        t_o = np.einsum("a,iac,c,jcb,b->iajb", ol[0], og[1], ol[1], og[2], ol[2])
+        t_g = np.einsum("a,iac,c,jcb,b->iajb", gl[0], gg[1], gl[1], gg[2], gl[2])
+        theta = max(theta, float(np.max(np.abs(t_o - t_g)) / np.max(np.abs(t_o))))
+    return {"max_spectrum_err": spec, "max_theta_err": theta, "updates": n_updates,
+            "case": "teacher-forced chi=256 updates of the CPU-baseline sample, GPU vs oracle"}
+
+
+def run_config3(prec, steps: int):
+    """Three-site workload: GHZ prefix, then a depth-12 shifted brick of Haar
+    U(8) gates on n = 48, chi_max = 128, cutoff 1e-12, as one recorded program."""
+    import torch
+    from paper_1111_3124_gb300 import circuits as C
+    from paper_1111_3124_gb300.mps import MPS, Program, circuit_passes
+    c = C.CONFIGS[3]
+    layers = C.config_circuit(3)
+    m = MPS(c["n"], c["chi_max"], c["cutoff"], prec)
+    prog = Program([m], circuit_passes(layers))
+    prog.run()
+    m.sync()
+    ts = []
+    for _ in range(steps):
+        m.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prog.run()
+        m.sync()
+        ts.append(time.perf_counter() - t0)
+    lam = [m.schmidt(b) for b in range(0, c["n"] - 1, 7)]
+    out = {"workload": c["name"], "updates_per_step": prog.updates, "value": prog.updates / (sum(ts) / len(ts)),
+           "unit": "updates/s", "steps": steps, "warmup": 1, "prec": "split" if prec else "fp64",
+           "timing": "wall clock around mps_program_run + mps_sync"}
+    prog.close()
+    m.close()
+    del lam
+    return out
+
+
+def run_config4(prec, count: int, steps: int):
+    """Many circuits at once: the first `count` circuits of the 512-circuit
+    workload (n in [16, 64], depth in [8, 24], chi_max in {32, 64, 128, 256},
+    Haar U(4) brickwork), recorded as one program whose passes hold the same
+    depth's layer of every circuit."""
+    import torch
+    from paper_1111_3124_gb300 import circuits as C
+    from paper_1111_3124_gb300.mps import MPS, Program
+    specs = C.batch_specs(512)[:count]
+    circuits = [C.batch_circuit(i, n, d) for i, (n, d, _) in enumerate(specs)]
+    states = [MPS(n, chi, 1e-12, prec) for n, _, chi in specs]
+    passes = []
+    for depth in range(max(d for _, d, _ in specs)):
+        gates, mats = [], []
+        for i, layers in enumerate(circuits):
+            if depth < len(layers):
+                for site, U in layers[depth]:
+                    gates.append((i, site))
+                    mats.append(U)
+        if gates:
+            passes.append((2, gates, torch.from_numpy(np.stack(mats).astype(np.complex128)).cuda()))
+    prog = Program(states, passes)
+    prog.run()
+    states[0].sync()
+    ts = []
+    for _ in range(steps):
+        for st in states:
+            st.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prog.run()
+        for st in states:
+            st.sync()
+        ts.append(time.perf_counter() - t0)
+    out = {"workload": "first %d of batch512_n16-64_d8-24_chi32-256" % count, "circuits": count,
+           "updates_per_step": prog.updates, "value": prog.updates / (sum(ts) / len(ts)), "unit": "updates/s",
+           "steps": steps, "warmup": 1, "prec": "split" if prec else "fp64",
+           "timing": "wall clock around mps_program_run + mps_sync of every circuit"}
+    prog.close()
+    for st in states:
+        st.close()
+    return out
+
+
 def run_gpu(a):
     import torch
     import torch.distributed as dist
@@ -284,22 +400,32 @@ def run_gpu(a):
         B.build()
     barrier()
     B.build()
-    from paper_1111_3124_gb300.mps import MPS, PREC_FP64, PREC_SPLIT
+    from paper_1111_3124_gb300.mps import MPS, PREC_FP64, PREC_SPLIT, Program
 
     c, layers, nup = workload()
     glayers = grouped(layers)
     dev_layers = [(k, s, torch.from_numpy(U).to("cuda")) for k, s, U in glayers]
     stream = torch.cuda.Stream()
-    m = MPS(c["n"], c["chi_max"], c["cutoff"], PREC_SPLIT if a.prec == "split" else PREC_FP64)
+    prec = PREC_SPLIT if a.prec == "split" else PREC_FP64
+    m = MPS(c["n"], c["chi_max"], c["cutoff"], prec)
     m.set_stream(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def step_device():
-        m.reset()
+    def step_eager(mm):
+        mm.reset()
         for k, s, dU in dev_layers:
-            m.apply_layer_device(s, dU, k)
+            mm.apply_layer_device(s, dU, k)
 
     with torch.cuda.stream(stream):
+        prog = Program([m], program_passes(dev_layers)) if a.path == "program" else None
+
+        def step_device():
+            if prog is None:
+                step_eager(m)
+            else:
+                m.reset()
+                prog.run()
+
         for _ in range(a.warmup):
             step_device()
         m.sync()
@@ -310,7 +436,6 @@ def run_gpu(a):
         chi = m.bond_dims()
         barrier()
         # ---- device-resident timed region
-        m.profile(True)
         times = []
         with ClockSampler(local) as clk:
             for _ in range(a.steps):
@@ -323,6 +448,16 @@ def run_gpu(a):
                 torch.cuda.synchronize()
                 times.append(e0.elapsed_time(e1))
         clocks = clk.summary()
+        m.sync()
+        # ---- per-kernel-class durations: CUDA events around every launch of
+        # one eager step on the same stream (a graph replay cannot be bracketed
+        # per kernel); the same kernels at the same sizes as the timed steps
+        flush.fill_(0.5)
+        m.profile(True)
+        t_prof0 = time.perf_counter()
+        step_eager(m)
+        m.sync()
+        t_prof = time.perf_counter() - t_prof0
         prof = {kk: m.profile_read(kk) for kk in range(len(KERNEL_CLASSES))}
         m.profile(False)
         # ---- end to end through the public API with host buffers
@@ -342,38 +477,46 @@ def run_gpu(a):
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
 
-    # ---- the native binary64 path on the same workload (one warm-up, one
-    # timed step) and the split result's deviation from it
+    # ---- the native binary64 path on the same workload and the split
+    # result's deviation from it
     fp64 = None
     if a.prec == "split" and not a.no_fp64_compare:
         with torch.cuda.stream(stream):
             m2 = MPS(c["n"], c["chi_max"], c["cutoff"], PREC_FP64)
             m2.set_stream(stream)
+            prog64 = Program([m2], program_passes(dev_layers)) if a.path == "program" else None
 
             def step64():
-                m2.reset()
-                for k, s, dU in dev_layers:
-                    m2.apply_layer_device(s, dU, k)
+                if prog64 is None:
+                    step_eager(m2)
+                else:
+                    m2.reset()
+                    prog64.run()
 
             step64()
             m2.sync()
-            flush.fill_(-1.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            step64()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t64 = e0.elapsed_time(e1) / 1e3
+            t64s = []
+            for _ in range(a.fp64_steps):
+                flush.fill_(-1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                step64()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t64s.append(e0.elapsed_time(e1) / 1e3)
+            t64 = sum(t64s) / len(t64s)
             bits = np.random.default_rng(11).integers(0, 2, size=(256, c["n"])).astype(np.uint8)
             a_sp, a_64 = m.amplitudes(bits), m2.amplitudes(bits)
             spec = max(float(np.max(np.abs(m.schmidt(b) - m2.schmidt(b)))) / float(np.max(m2.schmidt(b)))
                        if len(m.schmidt(b)) == len(m2.schmidt(b)) else float("inf") for b in range(c["n"] - 1))
-            fp64 = {"value": nup / t64, "unit": "updates/s", "ms_per_step": 1e3 * t64, "steps": 1, "warmup": 1,
-                    "split_speedup": None,
+            fp64 = {"value": nup / t64, "unit": "updates/s", "ms_per_step": 1e3 * t64, "steps": len(t64s),
+                    "warmup": 1, "step_ms": [1e3 * t for t in t64s], "split_speedup": None,
                     "split_vs_fp64": {"max_abs_amp_err": float(np.max(np.abs(a_sp - a_64))),
                                       "max_rel_amp_err": float(np.max(np.abs(a_sp - a_64)) / np.max(np.abs(a_64))),
                                       "max_spectrum_err": spec, "amplitudes_sampled": int(len(bits))}}
+            if prog64 is not None:
+                prog64.close()
             m2.close()
 
     t_step = sum(times) / len(times) / 1e3
@@ -384,11 +527,11 @@ def run_gpu(a):
 
     pk = peaks()
     roof_def = {  # class -> (kernel, bound, peak TFLOP/s, peak source)
-        0: ("k_jacobi_pair<double> (blocked one-sided Jacobi, binary64)", "alu", pk["fp64_tflops"],
+        0: ("k_jacobi_pair<8,double> (blocked one-sided Jacobi, binary64)", "alu", pk["fp64_tflops"],
             "binary64 ALU: 152 SMs x 2 FMA/clk x max SM clock"),
         1: ("k_contract (theta, binary64)", "alu", pk["fp64_tflops"], "binary64 ALU: unit counts x clock"),
         3: ("k_oz_gemm (split-precision bf16 tcgen05 GEMM)", "tensor", pk["bf16_tflops"], pk["bf16_source"]),
-        4: ("k_jacobi_pair<float> (fp32 preconditioning sweeps)", "alu", pk["fp32_tflops"],
+        4: ("k_jacobi_pair_f32<16> (fp32 preconditioning sweeps)", "alu", pk["fp32_tflops"],
             "fp32 ALU: 152 SMs x 128 FMA/clk x max SM clock"),
     }
     dom = max(roof_def, key=lambda i: prof[i]["ms"])
@@ -397,18 +540,21 @@ def run_gpu(a):
     name, bound, peak, src = roof_def[dom]
     # DRAM bytes per launch from one ncu capture of a saturated chi=256 layer
     # (the --profile-layer case), scaled to this run's average launch by
-    # duration (both kernels are ALU-bound: time tracks work)
-    captured = {0: (390.9e6, 2.2237), 4: (137.7e6, 0.2885)}  # class -> (bytes, ms) per launch
+    # duration (both Jacobi kernels are ALU-bound: time tracks work)
+    captured = {0: (390.9e6, 2.2237), 4: (146.0e6, 0.1697)}  # class -> (bytes, ms) per launch
     ms_launch = d["ms"] / max(d["launches"], 1)
     traffic = captured[dom][0] * ms_launch / captured[dom][1] if dom in captured else None
     roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if achieved else None, "peak_source": src,
             "flops_per_launch": d["flops"] / max(d["launches"], 1),
+            "flops_counted": "executed flops counted on the device (Gram, inner rotations, column rotations)"
+            if dom in (0, 4) else "tensor-core flops of the slice products",
             "ms_per_launch": ms_launch, "traffic": traffic,
             "traffic_source": "ncu dram__bytes_read+write of a saturated launch, scaled by duration"
             if traffic is not None else None,
-            "share_of_step": d["ms"] / (1e3 * t_step * a.steps)}
-    kernels = {name: {"ms_per_step": prof[i]["ms"] / a.steps, "launches_per_step": prof[i]["launches"] / a.steps,
+            "timing": "CUDA events around every launch of one eager step on the handle's stream",
+            "share_of_step": d["ms"] / (1e3 * t_prof)}
+    kernels = {name: {"ms_per_step": prof[i]["ms"], "launches_per_step": prof[i]["launches"],
                       "tflops": prof[i]["flops"] / (prof[i]["ms"] / 1e3) / 1e12 if prof[i]["ms"] > 0 else None}
                for i, name in enumerate(KERNEL_CLASSES)}
     line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": a.steps,
@@ -417,28 +563,40 @@ def run_gpu(a):
             "data": "synthetic (seeded Haar U(4) brickwork + RZ)",
             "config": {"workload": c["name"], "n": c["n"], "depth": c["depth"], "chi_max": c["chi_max"],
                        "cutoff": c["cutoff"], "updates_per_step": nup, "prec": a.prec,
+                       "path": "recorded program (one CUDA graph per step)" if a.path == "program"
+                       else "eager (host-driven passes)",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MiB buffer written between timed steps; working set > L2",
                        "max_bond": int(max(chi)) if len(chi) else 1},
             "roofline": roof, "kernels": kernels, "clocks": clocks,
-            "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "path": "mps_apply_layer with host gates (eager), D2H of the middle bond's Lambda"},
             "gpu_launches": int(prof[0]["launches_all"])}
     if fp64 is not None:
         fp64["split_speedup"] = value / world / fp64["value"]
         line["fp64_path"] = fp64
     if nominal:
-        # nominal binary64 work (theta GEMM + Golub-Reinsch SVD count) per second
-        # against the native binary64 peak: the effective binary64 rate of the path
+        # nominal binary64 work (theta GEMM + Golub-Reinsch SVD count) per second:
+        # what a binary64 Golub-Reinsch SVD path would have to sustain to match
         line["nominal_binary64"] = {
             "gflop_per_step": nominal / 1e9, "tflops": nominal / t_step / 1e12,
             "peak_fp64_tflops": pk["fp64_tflops"], "frac_of_fp64_peak": nominal / t_step / 1e12 / pk["fp64_tflops"],
-            "definition": "per update 8*M*N*chi + 4*(14*M*N^2 + 8*N^3), theta M x N = 2chi_L x 2chi_R"}
+            "definition": "reference-algorithm-equivalent rate, not executed flops: per update 8*M*N*chi + "
+                          "4*(14*M*N^2 + 8*N^3), theta M x N = 2chi_L x 2chi_R"}
         if fp64 is not None:
             fp64["nominal_binary64_tflops"] = nominal / (fp64["ms_per_step"] / 1e3) / 1e12
-    if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_obj(a.cpu_sample)
+    if rank == 0 and world == 1:
+        if not a.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_obj(a.cpu_sample)
+            line["oracle_check"] = {"split": oracle_check(PREC_SPLIT, a.cpu_sample),
+                                    "fp64": oracle_check(PREC_FP64, a.cpu_sample)}
+        if not a.no_extra_configs:
+            line["three_site"] = run_config3(prec, 2)
+            line["many_circuits"] = run_config4(prec, a.batch_circuits, 1)
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if prog is not None:
+        prog.close()
     m.close()
     if world > 1:
         dist.destroy_process_group()

@@ -298,6 +298,45 @@ int mps_profile(mps_handle h, int enable);
 int mps_profile_read(mps_handle h, int kernel, double* ms, long long* launches, double* flops,
                      long long* launches_all);
 
+/* A recorded circuit: passes of gate updates over one or more MPS, replayed
+ * as one CUDA graph (no paper counterpart: the batched, graph-captured form
+ * of the Sec. 3.1 update; many circuits at once is the batched workload).
+ * A program holds copies of its gates, the task tables of every pass and its
+ * own workspace; it must be destroyed before its handles. */
+typedef struct mps_program* mps_program_handle;
+
+/* mps_program_create - records n_passes passes. Pass p applies n_gates[p]
+ * gates of k[p] qubits (1, 2 or 3); gate g of the concatenation over passes
+ * acts on handle handles[owners[g]] (owners may be NULL when count = 1) at
+ * qubits sites[g] .. sites[g] + k - 1, and the gates of one pass are disjoint
+ * within each handle. d_Us: DEVICE memory holding every gate, 2^k x 2^k
+ * complex128 row-major, pass after pass (copied at creation). The work runs on
+ * handles[0]'s stream with its arithmetic mode; k = 1 gates are applied as
+ * they come (not held back).
+ * The recording needs no host synchronisation at replay: grids are sized for
+ * the bond bounds min(chi_max, 2 chi_l, 2 chi_r) that follow from every
+ * handle's bonds at creation, the Jacobi sweep loops are conditional (while)
+ * nodes whose continuation the device sets after each sweep (bounded by the
+ * sweep limits), and the task tables are built once. Recording applies
+ * nothing; held-back single-qubit gates of the handles are applied first.
+ * Errors: MPS_ERR_ARG, MPS_ERR_NOMEM, MPS_ERR_CUDA. */
+int mps_program_create(int count, const mps_handle* handles, int n_passes, const int* k, const int* n_gates,
+                       const int* sites, const int* owners, const double* d_Us, mps_program_handle* out);
+
+/* mps_program_run - replays the program on handles[0]'s stream, from the
+ * handles' current states (the other handles' streams are ordered before and
+ * after it). Every bond must be within the bound it had when the program was
+ * recorded (true after mps_reset for a program recorded from |0...0>), else
+ * MPS_ERR_ARG. Asynchronous: a deferred device error (MPS_ERR_NOCONVERGE on
+ * handles[0]) surfaces at the next synchronising call. */
+int mps_program_run(mps_program_handle p);
+
+/* Two- and three-site updates a run of the program performs. */
+int mps_program_updates(mps_program_handle p, long long* updates);
+
+/* Releases the program (waits for handles[0]'s stream). NULL is accepted. */
+int mps_program_destroy(mps_program_handle p);
+
 /* mps_sync - waits for the handle's stream and reports a deferred device
  * error (MPS_ERR_NOCONVERGE, MPS_ERR_TIMEOUT, MPS_ERR_CUDA), clearing it. */
 int mps_sync(mps_handle h);

@@ -99,6 +99,10 @@ struct mps_state {
   int prec = MPS_PREC_FP64, slices = 8, svd_mode = 0;
   int max_sweeps = kMaxSweeps;  // binary64 Jacobi sweep limit (mps_set_limits)
   int rot_tc = 0;               // fp32 sweeps rotate on the tensor cores (k_rot_tc) instead of in the pair kernel
+  // recording a program (mps_program_create): launches go into a CUDA graph,
+  // no host synchronisation, loops become conditional nodes captured on `side`
+  int capturing = 0;
+  cudaStream_t side = nullptr;
   cudaStream_t own = nullptr, stream = nullptr;
   double2* gamma = nullptr;
   double* lambda = nullptr;
@@ -151,6 +155,35 @@ struct mps_state {
   size_t ro_bytes = 0;
 };
 
+// A recorded circuit (mps_program_create): passes of gate updates over one or
+// more MPS, replayed as one CUDA graph. The program owns copies of the gates,
+// the task tables of every pass, and a workspace (arena, split-GEMM buffers)
+// sized for its largest pass.
+struct mps_program {
+  struct Chunk {
+    int k = 0;
+    std::vector<int> owner, site;  // the pass's gates: handle index, first site
+    GateTask* d_tasks = nullptr;   // k >= 2
+    TaskMeta* d_meta = nullptr;
+    SiteTask* d_site = nullptr;    // k = 1
+  };
+  std::vector<mps_state*> hs;
+  std::vector<Chunk> chunks;
+  std::vector<std::vector<int>> ub_start, ub_end;  // per handle: bond bounds the graph was sized for / leaves
+  bool split = false;
+  void* mem = nullptr;  // gates and tables
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  OzBuffers oz;
+  OzJob* d_jobs = nullptr;
+  int jobs_cap = 0;
+  cudaStream_t side = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long updates = 0;
+  long long recorded_launches = 0;  // kernels recorded (a loop body counted once)
+};
+
 namespace {
 
 size_t gamma_elems(const mps_state* h) { return (size_t)h->n * 2 * h->cap * h->cap; }
@@ -160,7 +193,7 @@ double* bond_ptr(const mps_state* h, int b) { return h->lambda + (size_t)(b + 1)
 // Profiling brackets: pbeg records a start event (profiling on) and returns its
 // index; pend records the end event and counts the launches of the class.
 int pbeg(mps_state* h) {
-  if (!h->prof) return -1;
+  if (!h->prof || h->capturing) return -1;
   if (h->ev_next + 2 > h->evs.size()) {
     for (int i = 0; i < 256; ++i) {
       cudaEvent_t e;
@@ -402,18 +435,99 @@ int flush_pending(mps_state* h) {
   return MPS_OK;
 }
 
+// ----------------------------------------------------------- device loops ---
+
+// Sets the condition of a while node from the continuation flag d_counter[0]
+// (tasks still active) and an iteration bound: the loop ends when no task is
+// active or after max_iter passes, whichever comes first.
+__global__ void k_loop_first(cudaGraphConditionalHandle hc, const int* flag, int* iter) {
+  *iter = 0;
+  cudaGraphSetConditional(hc, *flag > 0 ? 1u : 0u);
+}
+__global__ void k_loop_next(cudaGraphConditionalHandle hc, const int* flag, int* iter, int max_iter) {
+  const int it = ++*iter;
+  cudaGraphSetConditional(hc, (*flag > 0 && it < max_iter) ? 1u : 0u);
+}
+
+// Runs body() (one pass that leaves the number of still-active tasks in
+// d_counter[0]) while that number is non-zero, at most max_iter times.
+// first_always: the first pass runs unconditionally; otherwise d_counter[0]
+// already holds the count that decides it.
+// Eager: the host reads the count back after every pass. While recording a
+// program: a conditional while node whose body is one pass, recorded on the
+// side stream, with the device setting the node's condition (no host round trip).
+template <class F>
+int device_loop(mps_state* h, int max_iter, bool first_always, F body) {
+  if (!h->capturing) {
+    if (!first_always) {
+      CK(cudaMemcpyAsync(h->h_counter, h->d_counter, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      if (*h->h_counter == 0) return MPS_OK;
+    }
+    for (int it = 0; it < max_iter; ++it) {
+      const int rc = body();
+      if (rc) return rc;
+      CK(cudaMemcpyAsync(h->h_counter, h->d_counter, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      if (*h->h_counter == 0) break;
+    }
+    return MPS_OK;
+  }
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaGraphConditionalHandle hc;
+  CK(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return fail(MPS_ERR_CUDA, "device loop outside an active capture");
+  if (first_always) {
+    CK(cudaGraphConditionalHandleCreate(&hc, g, 1u, cudaGraphCondAssignDefault));
+    CK(cudaMemsetAsync(h->d_counter + 2, 0, sizeof(int), h->stream));
+  } else {
+    CK(cudaGraphConditionalHandleCreate(&hc, g, 0u, 0));
+    k_loop_first<<<1, 1, 0, h->stream>>>(hc, h->d_counter, h->d_counter + 2);
+    CK(cudaGetLastError());
+  }
+  CK(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = hc;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+  cudaGraph_t body_graph = np.conditional.phGraph_out[0];
+  CK(cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  CK(cudaStreamBeginCaptureToGraph(h->side, body_graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  cudaStream_t main = h->stream;
+  h->stream = h->side;
+  int rc = body();
+  if (!rc) {
+    k_loop_next<<<1, 1, 0, h->side>>>(hc, h->d_counter, h->d_counter + 2, max_iter);
+    if (cudaGetLastError() != cudaSuccess) rc = fail(MPS_ERR_CUDA, "loop condition launch");
+  }
+  h->stream = main;
+  cudaGraph_t out = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(h->side, &out);
+  if (rc) return rc;
+  if (ee != cudaSuccess) return fail(MPS_ERR_CUDA, std::string("loop body capture: ") + cudaGetErrorString(ee));
+  return MPS_OK;
+}
+
 // Blocked one-sided Jacobi on every task's working matrix (A, or T for the
 // second split of a three-site update). One launch per round-robin round;
 // a sweep ends with a convergence count read back to the host.
-int run_svd_on(mps_state* h, const GateTask* dt, TaskMeta* dm, int ntask, int nw_ub, int second, bool init_v);
+int run_svd_on(mps_state* h, const GateTask* dt, TaskMeta* dm, int ntask, int nw_ub, int second, bool init_v,
+               bool first_always = true);
 
-int run_svd(mps_state* h, int ntask, int nw_ub, int second, bool init_v = true) {
-  return run_svd_on(h, h->d_tasks, h->d_meta, ntask, nw_ub, second, init_v);
+int run_svd(mps_state* h, int ntask, int nw_ub, int second, bool init_v = true, bool first_always = true) {
+  return run_svd_on(h, h->d_tasks, h->d_meta, ntask, nw_ub, second, init_v, first_always);
 }
 
 // Jacobi sweeps on an explicit task/meta array (the layer's tasks, or the
 // sketch's small sub-problems).
-int run_svd_on(mps_state* h, const GateTask* dt, TaskMeta* dm, int ntask, int nw_ub, int second, bool init_v) {
+int run_svd_on(mps_state* h, const GateTask* dt, TaskMeta* dm, int ntask, int nw_ub, int second, bool init_v,
+               bool first_always) {
   if (init_v) {
     launch_init_V(dt, dm, ntask, nw_ub, h->stream);
     h->launches_all += 1;
@@ -421,19 +535,19 @@ int run_svd_on(mps_state* h, const GateTask* dt, TaskMeta* dm, int ntask, int nw
   const int nb = (nw_ub + kBlockW - 1) / kBlockW;
   const int nbe = nb + (nb & 1);
   unsigned long long* fl = h->prof ? h->d_prof_flops : nullptr;
-  for (int sw = 0; sw < h->max_sweeps; ++sw) {
+  const int max_sweeps = h->max_sweeps;
+  int rc = device_loop(h, max_sweeps, first_always, [&]() -> int {
     for (int r = 0; r < nbe - 1; ++r) {
       const int ev = pbeg(h);
       launch_jacobi_round(dt, dm, ntask, r, nbe / 2, second, fl, h->stream);
       pend(h, 0, ev, 1);
     }
     CK(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
-    launch_sweep_end(dm, ntask, h->max_sweeps, h->d_counter, h->stream);
+    launch_sweep_end(dm, ntask, max_sweeps, h->d_counter, h->stream);
     h->launches_all += 1;
-    CK(cudaMemcpyAsync(h->h_counter, h->d_counter, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    if (*h->h_counter == 0) break;
-  }
+    return MPS_OK;
+  });
+  if (rc) return rc;
   CK(cudaGetLastError());
   return MPS_OK;
 }
@@ -475,6 +589,8 @@ int oz_gemm(mps_state* h, int ng, int kind, int M_ub, int N_ub, int K_ub, int sl
   int rc0 = ensure_oz(h, ng);
   if (rc0) return rc0;
   const int sl = slices > 0 ? std::min(slices, h->slices) : h->slices;
+  if (h->capturing && OzBuffers::bytes_needed(ng, M_ub, N_ub, std::min(K_ub, 512), sl) > h->oz_buf.bytes)
+    return fail(MPS_ERR_CUDA, "recording: the split-GEMM buffers were sized too small");  // never reallocate mid-capture
   launch_oz_jobs(h->d_tasks, h->d_meta, h->d_oz_jobs, ng, kind, h->stream);
   const int ev = pbeg(h);
   const int rc = ozaki_zgemm(h->d_oz_jobs, ng, M_ub, N_ub, K_ub, sl, h->oz_buf, h->d_oz_err, h->stream);
@@ -494,7 +610,7 @@ int run_f32_sweeps(mps_state* h, int ng, int mw_ub, int nw_ub) {
   unsigned long long* fl = h->prof ? h->d_prof_flops + 4 : nullptr;
   // block rotations on the tensor cores once a pair's rows fill MMA tiles
   const bool tc = h->rot_tc && nw_ub >= kRotTcMinNw;
-  for (int sw = 0; sw < kF32Sweeps; ++sw) {
+  return device_loop(h, kF32Sweeps, true, [&]() -> int {
     for (int r = 0; r < nbe - 1; ++r) {
       const int ev = pbeg(h);
       launch_jacobi_round_f32(h->d_tasks, h->d_meta, ng, r, nbe / 2, kBlockW32, tc ? 0 : 1, fl, h->stream);
@@ -504,11 +620,8 @@ int run_f32_sweeps(mps_state* h, int ng, int mw_ub, int nw_ub) {
     CK(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->stream));
     launch_sweep_end_nofail(h->d_meta, ng, kF32Sweeps, h->d_counter, h->stream);
     h->launches_all += 1;
-    CK(cudaMemcpyAsync(h->h_counter, h->d_counter, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    if (*h->h_counter == 0) break;
-  }
-  return MPS_OK;
+    return MPS_OK;
+  });
 }
 
 // Split-precision theta and SVD of a layer of two-site gates (split_path.cu):
@@ -570,6 +683,12 @@ int run_split_svd(mps_state* h, int ng, int mw_ub, int nw_ub) {
     launch_givens(h->d_tasks, h->d_meta, ng, mw_ub + nw_ub, h->stream);
     pend(h, 5, ev, 2);
   }
+  if (h->capturing) {
+    // the blocked binary64 sweeps for the tasks the last Gram test left above
+    // the tolerance (their count is in d_counter[0]); a bounded wait that ran
+    // out is reported by the next synchronising call
+    return run_svd(h, ng, nw_ub, 0, false, false);
+  }
   int err = 0;
   CK(cudaMemcpyAsync(&err, h->d_oz_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(h->h_counter, h->d_counter, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -609,25 +728,35 @@ int read_meta(mps_state* w, int ng, std::vector<TaskMeta>& hm) {
   return MPS_OK;
 }
 
-int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const double2* d_U, int u_stride,
-                    bool split) {
-  const int ng = (int)refs.size();
-  int xl_ub = 1, x0_ub = 1, xr_ub = 1, nw_ub = 1, cap_ub = 1;
-  double fl_contract = 0.0;
-  std::vector<TaskLayout> lay(ng);
-  size_t total = 0;
-  for (int g = 0; g < ng; ++g) {
-    lay[g] = task_layout(refs[g], k, split);
-    total += lay[g].total;
+// Host bounds of the bonds a pass rewrites when the kept ranks are not read
+// back: the growth bounds min(chi_max, 2 chi_l, 2 chi_r) (two-site) and
+// min(chi_max, 2 chi_l, 4 chi_r), min(chi_max, 2 k1, 2 chi_r) (three-site).
+void advance_bounds(const std::vector<TaskRef>& refs, int k) {
+  for (const TaskRef& r : refs) {
+    mps_state* h = r.st;
+    const int s0 = r.site;
+    if (k == 2) {
+      h->ub[s0 + 1] = std::min(h->cap, std::min(2 * h->ub[s0], 2 * h->ub[s0 + 2]));
+    } else if (k == 3) {
+      const int k1 = std::min(h->cap, std::min(2 * h->ub[s0], 4 * h->ub[s0 + 3]));
+      h->ub[s0 + 1] = k1;
+      h->ub[s0 + 2] = std::min(h->cap, std::min(2 * k1, 2 * h->ub[s0 + 3]));
+    }
   }
-  int rc = ensure_arena(w, total);
-  if (rc) return rc;
-  unsigned char* base = static_cast<unsigned char*>(w->arena);
-  for (int g = 0; g < ng; ++g) {
+}
+
+// Fills the task table (w->h_tasks) of one pass with workspace carved from
+// `arena` by the tasks' layouts (from the current host bounds); returns the
+// workspace bytes used.
+size_t build_tasks(mps_state* w, int k, const std::vector<TaskRef>& refs, const double2* d_U, int u_stride,
+                   bool split, unsigned char* arena, GateTask* out) {
+  unsigned char* base = arena;
+  for (size_t g = 0; g < refs.size(); ++g) {
     mps_state* h = refs[g].st;
     const int s = refs[g].site;
+    const TaskLayout L = task_layout(refs[g], k, split);
     unsigned char* tb = base;
-    base += lay[g].total;
+    base += L.total;
     GateTask t;
     std::memset(&t, 0, sizeof(t));
     t.g0 = site_ptr(h, s);
@@ -643,7 +772,7 @@ int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const
     t.k = k;
     t.cap = h->cap;
     t.cutoff = h->cutoff;
-    const size_t* o = lay[g].off;
+    const size_t* o = L.off;
     t.A = reinterpret_cast<double2*>(tb + o[0]);
     t.V = reinterpret_cast<double2*>(tb + o[1]);
     t.T = reinterpret_cast<double2*>(tb + o[2]);
@@ -656,7 +785,27 @@ int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const
     t.V2 = reinterpret_cast<double2*>(tb + o[9]);
     t.Wp = reinterpret_cast<float2*>(tb + o[10]);
     t.Wneed = reinterpret_cast<int*>(tb + o[11]);
-    w->h_tasks[g] = t;
+    out[g] = t;
+  }
+  (void)w;
+  return (size_t)(base - arena);
+}
+
+// The launch sequence of one pass of k-site gate updates (k = 2, 3), possibly
+// from several MPS, on tasks already in w->d_tasks: theta, SVD, truncation,
+// rewrite. Grids are sized from the host bounds of the tasks' bonds.
+// Eager: reads the pass's task metadata back after the truncation (one small
+// copy) so that the bounds of the rewritten bonds become the kept ranks
+// themselves; the next layer's grids then follow the actual bond dimensions.
+// While recording a program: no read-back; the bounds advance by the growth
+// rule (advance_bounds).
+int emit_pass(mps_state* w, int k, const std::vector<TaskRef>& refs, bool split) {
+  const int ng = (int)refs.size();
+  int xl_ub = 1, x0_ub = 1, xr_ub = 1, nw_ub = 1, cap_ub = 1;
+  double fl_contract = 0.0;
+  for (int g = 0; g < ng; ++g) {
+    const mps_state* h = refs[g].st;
+    const int s = refs[g].site;
     const int xl = h->ub[s], x0 = h->ub[s + 1], xr = h->ub[s + k];
     xl_ub = std::max(xl_ub, xl);
     x0_ub = std::max(x0_ub, x0);
@@ -666,7 +815,7 @@ int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const
     if (k == 2) fl_contract += 32.0 * xl * x0 * xr + 128.0 * xl * xr;
     else fl_contract += 32.0 * x0 * h->ub[s + 2] * xr + 64.0 * xl * x0 * xr + 512.0 * xl * xr;
   }
-  CK(cudaMemcpyAsync(w->d_tasks, w->h_tasks, sizeof(GateTask) * ng, cudaMemcpyHostToDevice, w->stream));
+  int rc;
   launch_setup(w->d_tasks, w->d_meta, ng, 0, w->stream);
   w->launches_all += 1;
   if (split && k == 2) {
@@ -692,27 +841,31 @@ int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const
     launch_emit_left(w->d_tasks, w->d_meta, ng, xl_ub, k_ub, 0, w->stream);
     launch_emit_right(w->d_tasks, w->d_meta, ng, xr_ub, k_ub, 0, w->stream);
     pend(w, 2, ev, 4);
-    std::vector<TaskMeta> hm;
-    if ((rc = read_meta(w, ng, hm))) return rc;
-    for (int g = 0; g < ng; ++g) {
-      mps_state* h = refs[g].st;
-      const int bound = std::min(h->cap, std::min(2 * h->ub[refs[g].site], 2 * h->ub[refs[g].site + 2]));
-      h->ub[refs[g].site + 1] = hm[g].status == 0 ? std::max(1, std::min(bound, hm[g].knew)) : bound;
+    if (w->capturing) {
+      advance_bounds(refs, 2);
+    } else {
+      std::vector<TaskMeta> hm;
+      if ((rc = read_meta(w, ng, hm))) return rc;
+      for (int g = 0; g < ng; ++g) {
+        mps_state* h = refs[g].st;
+        const int bound = std::min(h->cap, std::min(2 * h->ub[refs[g].site], 2 * h->ub[refs[g].site + 2]));
+        h->ub[refs[g].site + 1] = hm[g].status == 0 ? std::max(1, std::min(bound, hm[g].knew)) : bound;
+      }
     }
   } else {
     launch_emit_left(w->d_tasks, w->d_meta, ng, xl_ub, k_ub, 0, w->stream);
     launch_form_second(w->d_tasks, w->d_meta, ng, k_ub, xr_ub, w->stream);
     launch_setup(w->d_tasks, w->d_meta, ng, 1, w->stream);
     pend(w, 2, ev, 5);
-    std::vector<TaskMeta> hm;
-    if ((rc = read_meta(w, ng, hm))) return rc;
     std::vector<int> k1s(ng);
     int nw2_ub = 1;
+    std::vector<TaskMeta> hm;
+    if (!w->capturing && (rc = read_meta(w, ng, hm))) return rc;
     for (int g = 0; g < ng; ++g) {
       const TaskRef& r = refs[g];
       const mps_state* h = r.st;
       const int bound = std::min(h->cap, std::min(2 * h->ub[r.site], 4 * h->ub[r.site + 3]));
-      k1s[g] = hm[g].status == 0 ? std::max(1, std::min(bound, hm[g].k1)) : bound;
+      k1s[g] = (!w->capturing && hm[g].status == 0) ? std::max(1, std::min(bound, hm[g].k1)) : bound;
       nw2_ub = std::max(nw2_ub, std::min(2 * k1s[g], 2 * h->ub[r.site + 3]));
     }
     launch_frob(w->d_tasks, w->d_meta, ng, (long long)(2 * k_ub) * (2 * xr_ub), 1, w->stream);
@@ -736,19 +889,35 @@ int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const
     launch_emit_left(w->d_tasks, w->d_meta, ng, k_ub, k2_ub, 1, w->stream);
     launch_emit_right(w->d_tasks, w->d_meta, ng, xr_ub, k2_ub, 1, w->stream);
     pend(w, 2, ev, 4);
-    if ((rc = read_meta(w, ng, hm))) return rc;
-    for (int g = 0; g < ng; ++g) {
-      mps_state* h = refs[g].st;
-      const int s0 = refs[g].site;
-      const int bound = std::min(h->cap, std::min(2 * k1s[g], 2 * h->ub[s0 + 3]));
-      h->ub[s0 + 1] = k1s[g];
-      h->ub[s0 + 2] = hm[g].status == 0 ? std::max(1, std::min(bound, hm[g].knew)) : bound;
+    if (w->capturing) {
+      advance_bounds(refs, 3);
+    } else {
+      if ((rc = read_meta(w, ng, hm))) return rc;
+      for (int g = 0; g < ng; ++g) {
+        mps_state* h = refs[g].st;
+        const int s0 = refs[g].site;
+        const int bound = std::min(h->cap, std::min(2 * k1s[g], 2 * h->ub[s0 + 3]));
+        h->ub[s0 + 1] = k1s[g];
+        h->ub[s0 + 2] = hm[g].status == 0 ? std::max(1, std::min(bound, hm[g].knew)) : bound;
+      }
     }
   }
   CK(cudaGetLastError());
   w->last_ntask = ng;
   w->last_k = k;
   return MPS_OK;
+}
+
+int run_update_refs(mps_state* w, int k, const std::vector<TaskRef>& refs, const double2* d_U, int u_stride,
+                    bool split) {
+  const int ng = (int)refs.size();
+  size_t total = 0;
+  for (int g = 0; g < ng; ++g) total += task_layout(refs[g], k, split).total;
+  int rc = ensure_arena(w, total);
+  if (rc) return rc;
+  build_tasks(w, k, refs, d_U, u_stride, split, static_cast<unsigned char*>(w->arena), w->h_tasks);
+  CK(cudaMemcpyAsync(w->d_tasks, w->h_tasks, sizeof(GateTask) * ng, cudaMemcpyHostToDevice, w->stream));
+  return emit_pass(w, k, refs, split);
 }
 
 // ------------------------------------------------------------- sketch path ---
@@ -1439,6 +1608,302 @@ int rdo_impl(mps_state* h, const int* qubits, int nq, std::vector<cd>& rho) {
   return MPS_OK;
 }
 
+// ---------------------------------------------------------------- programs ---
+
+constexpr int kProgMaxTasks = 512;  // gate tasks per recorded pass (bounds the split-GEMM buffers)
+
+void free_program(mps_program* p) {
+  if (!p) return;
+  if (!p->hs.empty() && p->hs[0]->stream) cudaStreamSynchronize(p->hs[0]->stream);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  cudaFree(p->mem);
+  cudaFree(p->arena);
+  cudaFree(p->oz.base);
+  cudaFree(p->d_jobs);
+  if (p->side) cudaStreamDestroy(p->side);
+  delete p;
+}
+
+// Upper bound of the split-GEMM buffers one pass needs (every product of the
+// split SVD, and theta for two-site gates, at the pass's bounds).
+size_t oz_bytes_for_pass(const std::vector<TaskRef>& refs, int k) {
+  int xl_ub = 1, x0_ub = 1, xr_ub = 1, nw_ub = 1, cap_ub = 1;
+  for (const TaskRef& r : refs) {
+    const mps_state* h = r.st;
+    xl_ub = std::max(xl_ub, h->ub[r.site]);
+    x0_ub = std::max(x0_ub, h->ub[r.site + 1]);
+    xr_ub = std::max(xr_ub, h->ub[r.site + k]);
+    cap_ub = std::max(cap_ub, h->cap);
+    nw_ub = std::max(nw_ub, std::min(2 * h->ub[r.site], (k == 3 ? 4 : 2) * h->ub[r.site + k]));
+  }
+  const int mw_ub = k == 3 ? std::max(2 * xl_ub, 4 * xr_ub) : std::max(2 * xl_ub, 2 * xr_ub);
+  const int M = std::max(std::max(2 * xl_ub, mw_ub), nw_ub);
+  const int N = std::max(2 * xr_ub, nw_ub);
+  const int K = std::min(512, std::max(std::max(x0_ub, nw_ub), mw_ub));
+  return OzBuffers::bytes_needed((int)refs.size(), M, N, K, 8);
+}
+
+int program_create(int count, const mps_handle* hs, int n_passes, const int* k, const int* n_gates, const int* sites,
+                   const int* owners, const double* d_Us, mps_program** out) {
+  if (!out) return fail(MPS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !hs || n_passes < 0 || (n_passes > 0 && (!k || !n_gates || !sites || !d_Us)))
+    return fail(MPS_ERR_ARG, "bad arguments");
+  if (count > 1 && !owners) return fail(MPS_ERR_ARG, "owners is NULL for several handles");
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return fail(MPS_ERR_ARG, "NULL handle");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(MPS_ERR_ARG, "a handle appears twice");
+  }
+  mps_state* w = hs[0];
+  // ---- the passes, validated per handle
+  size_t tot = 0, gate_doubles = 0;
+  std::vector<size_t> gate_off(n_passes);
+  for (int p = 0; p < n_passes; ++p) {
+    if (k[p] < 1 || k[p] > 3 || n_gates[p] < 0) return fail(MPS_ERR_ARG, "bad pass");
+    std::vector<std::vector<char>> used(count);
+    for (int i = 0; i < count; ++i) used[i].assign(hs[i]->n, 0);
+    for (int g = 0; g < n_gates[p]; ++g) {
+      const int o = owners ? owners[tot + g] : 0, s0 = sites[tot + g];
+      if (o < 0 || o >= count) return fail(MPS_ERR_ARG, "owner out of range");
+      if (s0 < 0 || s0 + k[p] > hs[o]->n) return fail(MPS_ERR_ARG, "gate site out of range");
+      for (int j = 0; j < k[p]; ++j) {
+        if (used[o][s0 + j]) return fail(MPS_ERR_ARG, "gates of a pass overlap");
+        used[o][s0 + j] = 1;
+      }
+    }
+    gate_off[p] = gate_doubles;
+    gate_doubles += (size_t)n_gates[p] * 2 * (1 << k[p]) * (1 << k[p]);
+    tot += n_gates[p];
+  }
+  mps_program* P = new mps_program();
+  P->hs.assign(hs, hs + count);
+  P->split = w->prec == MPS_PREC_SPLIT;
+  for (int i = 0; i < count; ++i) P->split = P->split && hs[i]->cap <= kSplitMaxCap;
+  for (int i = 0; i < count; ++i) P->ub_start.push_back(hs[i]->ub);
+  auto restore_ub = [&]() {
+    for (int i = 0; i < count; ++i) hs[i]->ub = P->ub_start[i];
+  };
+  auto bad = [&](int rc) {
+    restore_ub();
+    free_program(P);
+    return rc;
+  };
+  // ---- planning: chunks, their bounds, the workspace they need
+  size_t g0 = 0, arena_max = 0, oz_max = 0, table_bytes = 0;
+  int tasks_max = 1;
+  for (int p = 0; p < n_passes; ++p) {
+    std::vector<TaskRef> refs;
+    std::vector<int> own, st;
+    for (int g = 0; g < n_gates[p]; ++g) {
+      const int o = owners ? owners[g0 + g] : 0;
+      refs.push_back(TaskRef{hs[o], sites[g0 + g]});
+      own.push_back(o);
+      st.push_back(sites[g0 + g]);
+    }
+    g0 += n_gates[p];
+    for (size_t c0 = 0; c0 < refs.size();) {
+      size_t c1 = c0, bytes = 0;
+      while (c1 < refs.size() && (int)(c1 - c0) < kProgMaxTasks) {
+        const size_t b = k[p] >= 2 ? task_layout(refs[c1], k[p], P->split).total : 0;
+        if (c1 > c0 && bytes + b > kArenaBudget) break;
+        bytes += b;
+        ++c1;
+      }
+      mps_program::Chunk ch;
+      ch.k = k[p];
+      ch.owner.assign(own.begin() + c0, own.begin() + c1);
+      ch.site.assign(st.begin() + c0, st.begin() + c1);
+      std::vector<TaskRef> part(refs.begin() + c0, refs.begin() + c1);
+      if (k[p] >= 2) {
+        arena_max = std::max(arena_max, bytes);
+        if (P->split) oz_max = std::max(oz_max, oz_bytes_for_pass(part, k[p]));
+        tasks_max = std::max(tasks_max, (int)part.size());
+        table_bytes += align256(sizeof(GateTask) * part.size()) + align256(sizeof(TaskMeta) * part.size());
+        advance_bounds(part, k[p]);
+        P->updates += (long long)part.size();
+      } else {
+        table_bytes += align256(sizeof(SiteTask) * part.size());
+      }
+      P->chunks.push_back(ch);
+      c0 = c1;
+    }
+  }
+  for (int i = 0; i < count; ++i) P->ub_end.push_back(hs[i]->ub);
+  restore_ub();
+  // ---- memory: gates, tables, workspace, split-GEMM buffers
+  const size_t gate_bytes = align256(sizeof(double) * std::max<size_t>(gate_doubles, 2));
+  cudaError_t e = dev_alloc(&P->mem, gate_bytes + table_bytes + 256);
+  if (e == cudaSuccess && arena_max) e = dev_alloc(&P->arena, arena_max);
+  if (e == cudaSuccess && oz_max) e = dev_alloc(&P->oz.base, oz_max);
+  if (e == cudaSuccess && P->split) e = dev_alloc((void**)&P->d_jobs, sizeof(OzJob) * tasks_max);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking);
+  if (e != cudaSuccess)
+    return bad(fail(e == cudaErrorMemoryAllocation ? MPS_ERR_NOMEM : MPS_ERR_CUDA,
+                    std::string("program memory: ") + cudaGetErrorString(e)));
+  P->arena_bytes = arena_max;
+  P->oz.bytes = oz_max;
+  P->jobs_cap = tasks_max;
+  if (!w->d_oz_err) {
+    if ((e = dev_alloc((void**)&w->d_oz_err, sizeof(int))) != cudaSuccess || (e = cudaMemset(w->d_oz_err, 0, sizeof(int))) != cudaSuccess)
+      return bad(fail(MPS_ERR_NOMEM, "split GEMM error word"));
+  }
+  double2* gates = static_cast<double2*>(P->mem);
+  if (gate_doubles &&
+      (e = cudaMemcpy(gates, d_Us, sizeof(double) * gate_doubles, cudaMemcpyDeviceToDevice)) != cudaSuccess)
+    return bad(fail(MPS_ERR_CUDA, std::string("copying the gates: ") + cudaGetErrorString(e)));
+  // ---- task tables (built with the bounds each chunk will see)
+  unsigned char* tab = static_cast<unsigned char*>(P->mem) + gate_bytes;
+  {
+    size_t ci = 0, gsum = 0;
+    for (int p = 0; p < n_passes; ++p) {
+      const int d = 1 << k[p];
+      size_t in_pass = 0;
+      while (in_pass < (size_t)n_gates[p]) {
+        mps_program::Chunk& ch = P->chunks[ci++];
+        const size_t ng = ch.site.size();
+        const double2* gU = gates + gate_off[p] / 2 + (size_t)d * d * in_pass;
+        std::vector<TaskRef> refs;
+        for (size_t g = 0; g < ng; ++g) refs.push_back(TaskRef{hs[ch.owner[g]], ch.site[g]});
+        if (ch.k >= 2) {
+          std::vector<GateTask> ht(ng);
+          build_tasks(w, ch.k, refs, gU, d * d, P->split, static_cast<unsigned char*>(P->arena), ht.data());
+          ch.d_tasks = reinterpret_cast<GateTask*>(tab);
+          tab += align256(sizeof(GateTask) * ng);
+          ch.d_meta = reinterpret_cast<TaskMeta*>(tab);
+          tab += align256(sizeof(TaskMeta) * ng);
+          if ((e = cudaMemcpy(ch.d_tasks, ht.data(), sizeof(GateTask) * ng, cudaMemcpyHostToDevice)) != cudaSuccess ||
+              (e = cudaMemset(ch.d_meta, 0, sizeof(TaskMeta) * ng)) != cudaSuccess)
+            return bad(fail(MPS_ERR_CUDA, "task tables"));
+          advance_bounds(refs, ch.k);
+        } else {
+          std::vector<SiteTask> hsite(ng);
+          for (size_t g = 0; g < ng; ++g) {
+            mps_state* h = refs[g].st;
+            hsite[g].g = site_ptr(h, refs[g].site);
+            hsite[g].chi = h->chi;
+            hsite[g].site = refs[g].site;
+            hsite[g].cap = h->cap;
+            hsite[g].U = gU + 4 * g;
+          }
+          ch.d_site = reinterpret_cast<SiteTask*>(tab);
+          tab += align256(sizeof(SiteTask) * ng);
+          if ((e = cudaMemcpy(ch.d_site, hsite.data(), sizeof(SiteTask) * ng, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bad(fail(MPS_ERR_CUDA, "site tables"));
+        }
+        in_pass += ng;
+        gsum += ng;
+      }
+    }
+    (void)gsum;
+  }
+  restore_ub();
+  // ---- record: every launch of every chunk into one graph on the worker's stream
+  jacobi_f32_prepare();
+  rot_tc_prepare();
+  if (ozaki_prepare()) return bad(fail(MPS_ERR_CUDA, "split GEMM set-up"));
+  int rc = flush_pending(w);
+  for (int i = 1; i < count && !rc; ++i) rc = flush_pending(hs[i]);
+  if (rc) return bad(rc);
+  for (int i = 0; i < count; ++i)
+    if ((e = cudaStreamSynchronize(hs[i]->stream)) != cudaSuccess) return bad(fail(MPS_ERR_CUDA, "stream sync"));
+  GateTask* saved_tasks = w->d_tasks;
+  TaskMeta* saved_meta = w->d_meta;
+  void* saved_arena = w->arena;
+  const size_t saved_arena_bytes = w->arena_bytes;
+  OzJob* saved_jobs = w->d_oz_jobs;
+  const int saved_oz_cap = w->oz_cap;
+  const OzBuffers saved_oz = w->oz_buf;
+  const int saved_prof = w->prof;
+  const int saved_ntask = w->last_ntask;
+  const long long saved_launches = w->launches_all;
+  w->arena = P->arena;
+  w->arena_bytes = P->arena_bytes;
+  w->d_oz_jobs = P->d_jobs;
+  w->oz_cap = P->jobs_cap;
+  w->oz_buf = P->oz;
+  w->prof = 0;
+  w->side = P->side;
+  w->capturing = 1;
+  e = cudaStreamBeginCapture(w->stream, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    for (const mps_program::Chunk& ch : P->chunks) {
+      std::vector<TaskRef> refs;
+      for (size_t g = 0; g < ch.site.size(); ++g) refs.push_back(TaskRef{hs[ch.owner[g]], ch.site[g]});
+      if (ch.k == 1) {
+        int el_ub = 1;
+        for (const TaskRef& r : refs) el_ub = std::max(el_ub, r.st->ub[r.site] * r.st->ub[r.site + 1]);
+        launch_apply1(ch.d_site, (int)refs.size(), el_ub, w->stream);
+      } else {
+        w->d_tasks = ch.d_tasks;
+        w->d_meta = ch.d_meta;
+        rc = emit_pass(w, ch.k, refs, P->split);
+        if (rc) break;
+      }
+    }
+    const cudaError_t ee = cudaStreamEndCapture(w->stream, &P->graph);
+    if (!rc && ee != cudaSuccess) rc = fail(MPS_ERR_CUDA, std::string("recording: ") + cudaGetErrorString(ee));
+  } else {
+    rc = fail(MPS_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+  }
+  w->capturing = 0;
+  w->side = nullptr;
+  w->d_tasks = saved_tasks;
+  w->d_meta = saved_meta;
+  w->arena = saved_arena;
+  w->arena_bytes = saved_arena_bytes;
+  w->d_oz_jobs = saved_jobs;
+  w->oz_cap = saved_oz_cap;
+  w->oz_buf = saved_oz;
+  w->prof = saved_prof;
+  w->last_ntask = saved_ntask;
+  P->recorded_launches = w->launches_all - saved_launches;
+  w->launches_all = saved_launches;
+  restore_ub();
+  cudaGetLastError();
+  if (rc) return bad(rc);
+  if ((e = cudaGraphInstantiate(&P->exec, P->graph, 0)) != cudaSuccess)
+    return bad(fail(MPS_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e)));
+  *out = P;
+  return MPS_OK;
+}
+
+int program_run(mps_program* P) {
+  if (!P) return fail(MPS_ERR_ARG, "NULL program");
+  const int count = (int)P->hs.size();
+  for (int i = 0; i < count; ++i) {
+    const mps_state* h = P->hs[i];
+    for (int b = 0; b <= h->n; ++b)
+      if (h->ub[b] > P->ub_start[i][b])
+        return fail(MPS_ERR_ARG, "a bond is above the bound the program was recorded with (reset the state)");
+  }
+  for (int i = 0; i < count; ++i) {
+    const int rc = flush_pending(P->hs[i]);
+    if (rc) return rc;
+  }
+  mps_state* w = P->hs[0];
+  cudaEvent_t ev;
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  for (int i = 1; i < count; ++i) {
+    cudaEventRecord(ev, P->hs[i]->stream);
+    cudaStreamWaitEvent(w->stream, ev, 0);
+  }
+  const cudaError_t e = cudaGraphLaunch(P->exec, w->stream);
+  if (e == cudaSuccess) {
+    cudaEventRecord(ev, w->stream);
+    for (int i = 1; i < count; ++i) cudaStreamWaitEvent(P->hs[i]->stream, ev, 0);
+  }
+  cudaEventDestroy(ev);
+  if (e != cudaSuccess) return fail(MPS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  for (int i = 0; i < count; ++i) {
+    P->hs[i]->ub = P->ub_end[i];
+    P->hs[i]->last_ntask = 0;
+  }
+  w->launches_all += P->recorded_launches;
+  return MPS_OK;
+}
+
 }  // namespace
 
 // ================================================================= C ABI ===
@@ -1471,8 +1936,8 @@ int mps_create(int n, int chi_max, double cutoff, mps_handle* out) {
   if ((e = dev_alloc((void**)&h->gamma, sizeof(double2) * gamma_elems(h))) != cudaSuccess) return bad(e);
   if ((e = dev_alloc((void**)&h->lambda, sizeof(double) * (size_t)(n + 1) * chi_max)) != cudaSuccess) return bad(e);
   if ((e = dev_alloc((void**)&h->chi, sizeof(int) * (n + 1))) != cudaSuccess) return bad(e);
-  if ((e = dev_alloc((void**)&h->d_counter, 2 * sizeof(int))) != cudaSuccess) return bad(e);
-  if ((e = cudaMemset(h->d_counter, 0, 2 * sizeof(int))) != cudaSuccess) return bad(e);
+  if ((e = dev_alloc((void**)&h->d_counter, 4 * sizeof(int))) != cudaSuccess) return bad(e);
+  if ((e = cudaMemset(h->d_counter, 0, 4 * sizeof(int))) != cudaSuccess) return bad(e);
   if ((e = host_alloc((void**)&h->h_counter, sizeof(int))) != cudaSuccess) return bad(e);
   int rc = reset_state(h);
   if (rc) { free_state(h); return rc; }
@@ -1784,6 +2249,24 @@ int mps_diag(mps_handle h, int cap, int* count, int* k, double* discarded, int* 
       if (k_sketch) k_sketch[i] = t[i].ksk;
     }
   }
+  return MPS_OK;
+}
+
+int mps_program_create(int count, const mps_handle* handles, int n_passes, const int* k, const int* n_gates,
+                       const int* sites, const int* owners, const double* d_Us, mps_program_handle* out) {
+  return program_create(count, handles, n_passes, k, n_gates, sites, owners, d_Us, out);
+}
+
+int mps_program_run(mps_program_handle p) { return program_run(p); }
+
+int mps_program_updates(mps_program_handle p, long long* updates) {
+  if (!p || !updates) return fail(MPS_ERR_ARG, "bad arguments");
+  *updates = p->updates;
+  return MPS_OK;
+}
+
+int mps_program_destroy(mps_program_handle p) {
+  free_program(p);
   return MPS_OK;
 }
 

@@ -462,17 +462,25 @@ __global__ void __launch_bounds__(256, 3)
 template <int BW, bool FUSED>
 static void launch_pair_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub,
                             unsigned long long* flops, cudaStream_t st) {
-  static bool attr = false;
   constexpr int bytes = (int)sizeof(JacobiSmem<BW>);
-  if (!attr) {
-    cudaFuncSetAttribute(k_jacobi_pair_f32<BW, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    attr = true;
-  }
   k_jacobi_pair_f32<BW, FUSED><<<dim3(pairs_ub, ntask), 256, bytes, st>>>(t, m, round, flops);
+}
+
+void jacobi_f32_prepare() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_jacobi_pair_f32<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(JacobiSmem<8>));
+  cudaFuncSetAttribute(k_jacobi_pair_f32<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(JacobiSmem<16>));
+  cudaFuncSetAttribute(k_jacobi_pair_f32<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(JacobiSmem<16>));
+  done = true;
 }
 
 void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub, int bw, int fused,
                              unsigned long long* flops, cudaStream_t st) {
+  jacobi_f32_prepare();
   if (bw == 8)
     launch_pair_f32<8, true>(t, m, ntask, round, pairs_ub, flops, st);
   else if (fused)

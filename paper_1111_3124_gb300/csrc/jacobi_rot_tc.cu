@@ -320,13 +320,16 @@ __global__ void __launch_bounds__(kRtThreads, 2)
   }
 }
 
+void rot_tc_prepare() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kRtSmem);
+  done = true;
+}
+
 void launch_rot_tc(const GateTask* t, const TaskMeta* m, int ntask, int round, int pairs_ub, int mw_ub, int nw_ub,
                    int* err, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kRtSmem);
-    attr = true;
-  }
+  rot_tc_prepare();
   const int mt_ub = (mw_ub + kRtRows - 1) / kRtRows + (nw_ub + kRtRows - 1) / kRtRows;
   k_rot_tc<<<dim3(pairs_ub * mt_ub, ntask), kRtThreads, kRtSmem, st>>>(t, m, round, mt_ub, err);
 }

@@ -36,6 +36,10 @@ void launch_sweep_end_nofail(TaskMeta* m, int ntask, int max_sweeps, int* active
 // (jacobi_rot_tc.cu) applies it to the rows of A32 and V32 on the tensor cores.
 void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub, int bw, int fused,
                              unsigned long long* flops, cudaStream_t st);
+// One-time kernel attributes (shared-memory sizes), set before a program
+// records launches into a graph; the launchers call them too.
+void jacobi_f32_prepare();
+void rot_tc_prepare();
 void launch_rot_tc(const GateTask* t, const TaskMeta* m, int ntask, int round, int pairs_ub, int mw_ub, int nw_ub,
                    int* err, cudaStream_t st);
 void launch_colnorms(const GateTask* t, const TaskMeta* m, int ntask, int nw_ub, int second, cudaStream_t st);

@@ -39,6 +39,9 @@ struct OzBuffers {
 // M_ub, N_ub, K_ub) with s slices per operand. Returns 0 or a negative code.
 // K above 512 runs in 512-wide chunks accumulated in binary64.
 // d_err: device int set to 1 if a bounded wait ran out.
+// One-time set-up of the GEMM kernel (0 on success); ozaki_zgemm calls it.
+int ozaki_prepare();
+
 int ozaki_zgemm(const OzJob* d_jobs, int njobs, int M_ub, int N_ub, int K_ub, int s, OzBuffers& buf, int* d_err,
                 cudaStream_t st);
 

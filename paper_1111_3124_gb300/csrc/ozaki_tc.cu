@@ -323,6 +323,17 @@ static int make_map(CUtensorMap* map, const __nv_bfloat16* base, int Kp, int row
 
 static inline int rup(int a, int b) { return (a + b - 1) / b * b; }
 
+// One-time set-up (the kernel's shared-memory attribute, the tensor-map
+// encoder): done before a program records launches into a graph.
+int ozaki_prepare() {
+  static bool done = false;
+  if (done) return 0;
+  if (encode_fn()) return -1;
+  if (cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem) != cudaSuccess) return -1;
+  done = true;
+  return 0;
+}
+
 size_t OzBuffers::bytes_needed(int jobs, int M_ub, int N_ub, int K_ub, int s) {
   const size_t Mp = rup(2 * M_ub, kOzM), Np = rup(N_ub, kOzN), Kp = rup(2 * K_ub, kOzK);
   return (size_t)jobs * s * (Mp + Np) * Kp * 2 + (size_t)jobs * (Mp / 2 + Np) * sizeof(int) + 4096;
@@ -355,11 +366,7 @@ int ozaki_zgemm(const OzJob* d_jobs, int njobs, int M_ub, int N_ub, int K_ub, in
   int* fb = reinterpret_cast<int*>(p);
   CUtensorMap mA, mB;
   if (make_map(&mA, Ah, Kp, Mp, s, njobs, kOzM) || make_map(&mB, Bh, Kp, Np, s, njobs, kOzN)) return -3;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem) != cudaSuccess) return -4;
-    attr = true;
-  }
+  if (ozaki_prepare()) return -4;
   for (int k0 = 0; k0 < K_ub; k0 += kchunk) {
     k_oz_split<<<dim3((Mp / 2 + 7) / 8, njobs), 256, 0, st>>>(d_jobs, 0, Ah, ea, Mp, Kp, s, k0, kchunk);
     k_oz_split<<<dim3((Np + 7) / 8, njobs), 256, 0, st>>>(d_jobs, 1, Bh, fb, Np, Kp, s, k0, kchunk);

@@ -36,6 +36,7 @@ EXPORTS = [
     "mps_gate2_update_noalloc", "mps_split_zgemm", "mps_apply_layer_multi",
     "mps_mlp_create", "mps_mlp_destroy", "mps_mlp_params", "mps_mlp_forward", "mps_mlp_loss_grad", "mps_mlp_train",
     "mps_layer_features", "mps_set_predictor", "mps_sketch_stats", "mps_set_limits", "mps_debug_fail_alloc",
+    "mps_program_create", "mps_program_run", "mps_program_updates", "mps_program_destroy",
 ]
 
 
@@ -96,6 +97,10 @@ def load_library(path: str = LIB_PATH):
         "mps_sketch_stats": [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_longlong)],
         "mps_set_limits": [P, I],
+        "mps_program_create": [I, ctypes.POINTER(P), I, ip, ip, ip, ip, P, ctypes.POINTER(P)],
+        "mps_program_run": [P],
+        "mps_program_updates": [P, ctypes.POINTER(ctypes.c_longlong)],
+        "mps_program_destroy": [P],
         "mps_debug_fail_alloc": [ctypes.c_longlong],
     }
     for name, args in sig.items():
@@ -317,6 +322,62 @@ class MPS:
                 if d >= 4:
                     nup += len(gs)
         return nup
+
+
+class Program:
+    """A recorded circuit over one or more MPS, replayed as one CUDA graph
+    (mps_program_create). passes: a list of (k, gates, d_Us), where gates is a
+    list of (owner, site) (owner indexes `states`) and d_Us a CUDA complex128
+    tensor of shape (len(gates), 2^k, 2^k)."""
+
+    def __init__(self, states, passes):
+        import torch
+        self._states = list(states)
+        ks = np.ascontiguousarray([k for k, _, _ in passes], dtype=np.int32)
+        ng = np.ascontiguousarray([len(g) for _, g, _ in passes], dtype=np.int32)
+        owners = np.ascontiguousarray([o for _, g, _ in passes for (o, _) in g] or [0], dtype=np.int32)
+        sites = np.ascontiguousarray([s for _, g, _ in passes for (_, s) in g] or [0], dtype=np.int32)
+        mats = [U.reshape(-1) for _, g, U in passes if len(g)]
+        self._gates = torch.cat(mats) if mats else torch.zeros(1, dtype=torch.complex128, device="cuda")
+        hs = (ctypes.c_void_p * len(states))(*[m._h.value for m in states])
+        h = ctypes.c_void_p()
+        check(load_library().mps_program_create(len(states), hs, len(passes), _ip(ks), _ip(ng), _ip(sites),
+                                                _ip(owners), ctypes.c_void_p(self._gates.data_ptr()),
+                                                ctypes.byref(h)))
+        self._h = h
+
+    def run(self) -> None:
+        check(load_library().mps_program_run(self._h))
+
+    @property
+    def updates(self) -> int:
+        u = ctypes.c_longlong()
+        check(load_library().mps_program_updates(self._h, ctypes.byref(u)))
+        return u.value
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load_library().mps_program_destroy(h)
+        self._h = None
+
+    __del__ = close
+
+
+def circuit_passes(layers, owner: int = 0, device="cuda"):
+    """A circuit given as layers of (site, U) as program passes: one pass per
+    layer and gate size, gates on the device."""
+    import torch
+    out = []
+    for layer in layers:
+        by_k = {}
+        for site, U in layer:
+            by_k.setdefault({2: 1, 4: 2, 8: 3}[U.shape[0]], []).append((site, U))
+        for k in sorted(by_k):
+            gs = by_k[k]
+            U = torch.from_numpy(np.ascontiguousarray(np.stack([_c128(u) for _, u in gs]))).to(device)
+            out.append((k, [(owner, s) for s, _ in gs], U))
+    return out
 
 
 def debug_fail_alloc(after: int) -> None:
