@@ -79,6 +79,7 @@ def args_parse():
     p.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the binary64 comparison")
     p.add_argument("--no-extra-configs", action="store_true", help="skip the three-site and many-circuit lines")
     p.add_argument("--batch-circuits", type=int, default=32, help="circuits of the many-circuit line")
+    p.add_argument("--retune", action="store_true", help="ignore the tuner's cache")
     p.add_argument("--chi", type=int, default=256, help="bond dimension of the saturated-layer case")
     p.add_argument("--layers", type=int, default=1, help="layers of the saturated-layer case")
     return p.parse_args()
@@ -306,7 +307,7 @@ def oracle_check(prec, n_updates: int):
             "case": "teacher-forced chi=256 updates of the CPU-baseline sample, GPU vs oracle"}
 
 
-def run_config3(prec, steps: int):
+def run_config3(prec, steps: int, tune_table=()):
     """Three-site workload: GHZ prefix, then a depth-12 shifted brick of Haar
     U(8) gates on n = 48, chi_max = 128, cutoff 1e-12, as one recorded program."""
     import torch
@@ -315,6 +316,7 @@ def run_config3(prec, steps: int):
     c = C.CONFIGS[3]
     layers = C.config_circuit(3)
     m = MPS(c["n"], c["chi_max"], c["cutoff"], prec)
+    m.set_tuning(list(tune_table))
     prog = Program([m], circuit_passes(layers))
     prog.run()
     m.sync()
@@ -336,7 +338,7 @@ def run_config3(prec, steps: int):
     return out
 
 
-def run_config4(prec, count: int, steps: int):
+def run_config4(prec, count: int, steps: int, tune_table=()):
     """Many circuits at once: the first `count` circuits of the 512-circuit
     workload (n in [16, 64], depth in [8, 24], chi_max in {32, 64, 128, 256},
     Haar U(4) brickwork), recorded as one program whose passes hold the same
@@ -347,6 +349,7 @@ def run_config4(prec, count: int, steps: int):
     specs = C.batch_specs(512)[:count]
     circuits = [C.batch_circuit(i, n, d) for i, (n, d, _) in enumerate(specs)]
     states = [MPS(n, chi, 1e-12, prec) for n, _, chi in specs]
+    states[0].set_tuning(list(tune_table))  # the program's work runs with the first handle's settings
     passes = []
     for depth in range(max(d for _, d, _ in specs)):
         gates, mats = [], []
@@ -415,6 +418,16 @@ def run_gpu(a):
         mm.reset()
         for k, s, dU in dev_layers:
             mm.apply_layer_device(s, dU, k)
+
+    # launch shapes of the fp32 sweeps per width: the cached tuner table, else tuned now
+    from paper_1111_3124_gb300 import tuner
+    tune_table = tuner.load() if not a.retune else None
+    tune_source = "cache " + tuner.cache_path()
+    if tune_table is None:
+        tune_table, _ = tuner.tune()
+        tuner.save(tune_table, _)
+        tune_source = "tuned in this run (" + tuner.cache_path() + ")"
+    m.set_tuning(tune_table)
 
     with torch.cuda.stream(stream):
         prog = Program([m], program_passes(dev_layers)) if a.path == "program" else None
@@ -567,6 +580,8 @@ def run_gpu(a):
                        else "eager (host-driven passes)",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MiB buffer written between timed steps; working set > L2",
+                       "tuning": {"table (nw_max, fp32 block, rotation on tensor cores)": tune_table,
+                                  "source": tune_source},
                        "max_bond": int(max(chi)) if len(chi) else 1},
             "roofline": roof, "kernels": kernels, "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -591,8 +606,8 @@ def run_gpu(a):
             line["oracle_check"] = {"split": oracle_check(PREC_SPLIT, a.cpu_sample),
                                     "fp64": oracle_check(PREC_FP64, a.cpu_sample)}
         if not a.no_extra_configs:
-            line["three_site"] = run_config3(prec, 2)
-            line["many_circuits"] = run_config4(prec, a.batch_circuits, 1)
+            line["three_site"] = run_config3(prec, 2, tune_table)
+            line["many_circuits"] = run_config4(prec, a.batch_circuits, 1, tune_table)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if prog is not None:

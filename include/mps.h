@@ -131,6 +131,16 @@ int mps_set_mode(mps_handle h, int prec, int slices, int svd_mode);
  * the next synchronising call. Errors: MPS_ERR_ARG. */
 int mps_set_limits(mps_handle h, int max_sweeps);
 
+/* mps_set_tuning - the launch shape of the split mode's fp32 sweeps per
+ * working-matrix width Nw (the smaller dimension of theta; no paper
+ * counterpart: chosen by measurement, see the package's tuner). Entry i
+ * applies to Nw <= nw_max[i] (increasing; the last entry also covers larger
+ * widths): f32_block[i] = 8 or 16 columns per block, rot_tc[i] = 1 applies the
+ * block rotations on the tensor cores (block width 16 only) instead of in the
+ * pair kernel. n = 0 restores the default (16, pair kernel). Host arrays.
+ * Errors: MPS_ERR_ARG. */
+int mps_set_tuning(mps_handle h, int n, const int* nw_max, const int* f32_block, const int* rot_tc);
+
 /* mps_debug_fail_alloc - test hook for the allocation-failure path (no paper
  * counterpart): the next `after` device or pinned-host allocations made by
  * the library succeed, the one after that is refused as if the device were out

@@ -99,6 +99,12 @@ struct mps_state {
   int prec = MPS_PREC_FP64, slices = 8, svd_mode = 0;
   int max_sweeps = kMaxSweeps;  // binary64 Jacobi sweep limit (mps_set_limits)
   int rot_tc = 0;               // fp32 sweeps rotate on the tensor cores (k_rot_tc) instead of in the pair kernel
+  // per working-matrix width: fp32 block width and rotation (mps_set_tuning);
+  // empty: block width 16, rotation in the pair kernel
+  struct Tune {
+    int nw_max, f32_block, rot_tc;
+  };
+  std::vector<Tune> tune;
   // recording a program (mps_program_create): launches go into a CUDA graph,
   // no host synchronisation, loops become conditional nodes captured on `side`
   int capturing = 0;
@@ -605,15 +611,21 @@ int oz_gemm(mps_state* h, int ng, int kind, int M_ub, int N_ub, int K_ub, int sl
 // fp32 preconditioning sweeps on (A32, V32) of every task, then re-arm the
 // tasks (the binary64 sweeps reuse the active/sweep counters).
 int run_f32_sweeps(mps_state* h, int ng, int mw_ub, int nw_ub) {
-  const int nb = (nw_ub + kBlockW32 - 1) / kBlockW32;
-  const int nbe = nb + (nb & 1);
   unsigned long long* fl = h->prof ? h->d_prof_flops + 4 : nullptr;
-  // block rotations on the tensor cores once a pair's rows fill MMA tiles
-  const bool tc = h->rot_tc && nw_ub >= kRotTcMinNw;
+  // the tuned choice for this width (block width, rotation on the tensor cores)
+  int bw = kBlockW32;
+  bool tc = h->rot_tc && nw_ub >= kRotTcMinNw;
+  for (const mps_state::Tune& t : h->tune) {
+    bw = t.f32_block;
+    tc = t.rot_tc != 0;
+    if (nw_ub <= t.nw_max) break;
+  }
+  const int nb = (nw_ub + bw - 1) / bw;
+  const int nbe = nb + (nb & 1);
   return device_loop(h, kF32Sweeps, true, [&]() -> int {
     for (int r = 0; r < nbe - 1; ++r) {
       const int ev = pbeg(h);
-      launch_jacobi_round_f32(h->d_tasks, h->d_meta, ng, r, nbe / 2, kBlockW32, tc ? 0 : 1, fl, h->stream);
+      launch_jacobi_round_f32(h->d_tasks, h->d_meta, ng, r, nbe / 2, bw, tc ? 0 : 1, fl, h->stream);
       if (tc) launch_rot_tc(h->d_tasks, h->d_meta, ng, r, nbe / 2, mw_ub, nw_ub, h->d_oz_err, h->stream);
       pend(h, 4, ev, tc ? 2 : 1);
     }
@@ -1975,6 +1987,21 @@ int mps_set_limits(mps_handle h, int max_sweeps) {
   if (max_sweeps < 1 || max_sweeps > kMaxSweeps) return fail(MPS_ERR_ARG, "max_sweeps must be 1..60");
   CK(cudaStreamSynchronize(h->stream));
   h->max_sweeps = max_sweeps;
+  return MPS_OK;
+}
+
+int mps_set_tuning(mps_handle h, int n, const int* nw_max, const int* f32_block, const int* rot_tc) {
+  if (!h) return fail(MPS_ERR_ARG, "NULL handle");
+  if (n < 0 || (n > 0 && (!nw_max || !f32_block || !rot_tc))) return fail(MPS_ERR_ARG, "bad table");
+  std::vector<mps_state::Tune> t(n);
+  for (int i = 0; i < n; ++i) {
+    if (f32_block[i] != 8 && f32_block[i] != 16) return fail(MPS_ERR_ARG, "fp32 block width must be 8 or 16");
+    if (rot_tc[i] && f32_block[i] != 16) return fail(MPS_ERR_ARG, "the tensor-core rotation needs block width 16");
+    if (i > 0 && nw_max[i] <= nw_max[i - 1]) return fail(MPS_ERR_ARG, "widths must increase");
+    t[i] = mps_state::Tune{nw_max[i], f32_block[i], rot_tc[i] ? 1 : 0};
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  h->tune = t;
   return MPS_OK;
 }
 

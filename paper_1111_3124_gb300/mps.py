@@ -36,7 +36,7 @@ EXPORTS = [
     "mps_gate2_update_noalloc", "mps_split_zgemm", "mps_apply_layer_multi",
     "mps_mlp_create", "mps_mlp_destroy", "mps_mlp_params", "mps_mlp_forward", "mps_mlp_loss_grad", "mps_mlp_train",
     "mps_layer_features", "mps_set_predictor", "mps_sketch_stats", "mps_set_limits", "mps_debug_fail_alloc",
-    "mps_program_create", "mps_program_run", "mps_program_updates", "mps_program_destroy",
+    "mps_program_create", "mps_program_run", "mps_program_updates", "mps_program_destroy", "mps_set_tuning",
 ]
 
 
@@ -97,6 +97,7 @@ def load_library(path: str = LIB_PATH):
         "mps_sketch_stats": [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_longlong)],
         "mps_set_limits": [P, I],
+        "mps_set_tuning": [P, I, ip, ip, ip],
         "mps_program_create": [I, ctypes.POINTER(P), I, ip, ip, ip, ip, P, ctypes.POINTER(P)],
         "mps_program_run": [P],
         "mps_program_updates": [P, ctypes.POINTER(ctypes.c_longlong)],
@@ -165,6 +166,13 @@ class MPS:
 
     def set_limits(self, max_sweeps: int) -> None:
         check(load_library().mps_set_limits(self._h, max_sweeps))
+
+    def set_tuning(self, table) -> None:
+        """table: list of (nw_max, f32_block, rot_tc), nw_max increasing."""
+        nw = np.ascontiguousarray([t[0] for t in table] or [0], dtype=np.int32)
+        bw = np.ascontiguousarray([t[1] for t in table] or [0], dtype=np.int32)
+        tc = np.ascontiguousarray([t[2] for t in table] or [0], dtype=np.int32)
+        check(load_library().mps_set_tuning(self._h, len(table), _ip(nw), _ip(bw), _ip(tc)))
 
     def apply_gate(self, site: int, U) -> None:
         U = _c128(U)
