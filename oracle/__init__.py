@@ -56,6 +56,8 @@ def lib():
         L.oracle_mps_get_state.argtypes = [P, ip, dp, dp]
         L.oracle_mps_last_diag.argtypes = [P, ip, dp, ip, ip]
         L.oracle_svd.argtypes = [I, I, I, dp, dp, dp, dp]
+        L.oracle_mps_sample.argtypes = [P, dp, ctypes.c_char_p]
+        L.oracle_mps_pauli.argtypes = [P, ctypes.c_char_p, dp]
         _lib = L
     return _lib
 
@@ -161,6 +163,22 @@ class OracleMPS:
         if rc != 0:
             raise RuntimeError("oracle rdo failed")
         return rho
+
+    def sample(self, u) -> np.ndarray:
+        """Bit strings (rows) from uniforms u (rows of n values in [0, 1))."""
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1, self.n))
+        out = np.zeros(u.shape, dtype=np.uint8)
+        buf = ctypes.create_string_buffer(self.n)
+        for r in range(u.shape[0]):
+            lib().oracle_mps_sample(self._h, _dp(u[r]), buf)
+            out[r] = np.frombuffer(buf.raw[:self.n], dtype=np.uint8)
+        return out
+
+    def pauli_expectation(self, p: str) -> complex:
+        assert len(p) == self.n and set(p) <= set("IXYZ")
+        out = np.zeros(2)
+        lib().oracle_mps_pauli(self._h, p.encode(), _dp(out))
+        return complex(out[0], out[1])
 
     def bond_dim(self, b: int) -> int:
         return lib().oracle_mps_bond_dim(self._h, b)

@@ -246,6 +246,8 @@ class OracleBase {
   virtual void amplitude(const unsigned char* bits, double* out) = 0;
   virtual int expectation(int site, int k, const double* O, double* out) = 0;
   virtual int rdo(const int* qubits, int nq, double* rho) = 0;
+  virtual void sample(const double* u, unsigned char* bits) = 0;
+  virtual void pauli(const char* p, double* out) = 0;
   virtual int bond(int b) const = 0;
   virtual void schmidt(int b, double* lam) const = 0;
   virtual int set_state(const int* chi, const double* gam, const double* lam) = 0;
@@ -593,6 +595,80 @@ class OracleMPS : public OracleBase {
     return 0;
   }
 
+  // Right environment through site s: R'[a,a'] = sum_i sum_{c,c'}
+  // (Gamma_s[i] Lambda_s)[a,c] R[c,c'] conj((Gamma_s[i] Lambda_s)[a',c']).
+  std::vector<Cx<R>> right_transfer(int s, const std::vector<Cx<R>>& Rr) const {
+    const int a_n = cl(s), c_n = cr(s);
+    std::vector<Cx<R>> out((size_t)a_n * a_n);
+    for (int i = 0; i < 2; ++i)
+      for (int a = 0; a < a_n; ++a)
+        for (int a2 = 0; a2 < a_n; ++a2) {
+          Cx<R> acc;
+          for (int c = 0; c < c_n; ++c)
+            for (int c2 = 0; c2 < c_n; ++c2)
+              acc = acc + ((lam(s)[c] * gc(s, i, a, c)) * Rr[(size_t)c * c_n + c2]) *
+                              conj(lam(s)[c2] * gc(s, i, a2, c2));
+          out[(size_t)a * a_n + a2] = out[(size_t)a * a_n + a2] + acc;
+        }
+    return out;
+  }
+
+  // One bit string by sequential conditional sampling of |<b|psi>|^2 /
+  // <psi|psi>: qubit s takes 0 when u[s] < p(b_s = 0 | b_0 .. b_{s-1}), else 1.
+  // The conditional weights contract the chosen prefix (a row vector v) with
+  // the right environments of the rest of the chain.
+  void sample(const double* u, unsigned char* bits) override {
+    std::vector<std::vector<Cx<R>>> env(n + 1);
+    env[n] = std::vector<Cx<R>>(1, Cx<R>(1));
+    for (int s = n - 1; s >= 0; --s) env[s] = right_transfer(s, env[s + 1]);
+    std::vector<Cx<R>> v(1, Cx<R>(1));
+    for (int s = 0; s < n; ++s) {
+      const int a_n = cl(s), c_n = cr(s);
+      std::vector<Cx<R>> w[2];
+      R p[2];
+      for (int i = 0; i < 2; ++i) {
+        w[i].assign(c_n, Cx<R>());
+        for (int c = 0; c < c_n; ++c) {
+          Cx<R> acc;
+          for (int a = 0; a < a_n; ++a) acc = acc + v[a] * gc(s, i, a, c);
+          w[i][c] = lam(s)[c] * acc;
+        }
+        Cx<R> q;
+        for (int c = 0; c < c_n; ++c)
+          for (int c2 = 0; c2 < c_n; ++c2) q = q + (w[i][c] * env[s + 1][(size_t)c * c_n + c2]) * conj(w[i][c2]);
+        p[i] = q.re;
+      }
+      const R p0 = p[0] / (p[0] + p[1]);
+      const int b = (R)u[s] < p0 ? 0 : 1;
+      bits[s] = (unsigned char)b;
+      const R inv = 1 / Num<R>::sqrt_(p[b]);
+      v.assign(c_n, Cx<R>());
+      for (int c = 0; c < c_n; ++c) v[c] = inv * w[b][c];
+    }
+  }
+
+  // <psi|P|psi> / <psi|psi> for a Pauli string P (one of I, X, Y, Z per
+  // qubit): the full transfer contraction with the Pauli matrix as the
+  // physical weight at every site.
+  void pauli(const char* ps, double* out) override {
+    const Cx<R> I2[4] = {Cx<R>(1), Cx<R>(), Cx<R>(), Cx<R>(1)};
+    const Cx<R> X2[4] = {Cx<R>(), Cx<R>(1), Cx<R>(1), Cx<R>()};
+    const Cx<R> Y2[4] = {Cx<R>(), Cx<R>(0, -1), Cx<R>(0, 1), Cx<R>()};
+    const Cx<R> Z2[4] = {Cx<R>(1), Cx<R>(), Cx<R>(), Cx<R>(-1)};
+    // W[i,j] weights ket index i against bra index j: <psi|P|psi> = sum P[j,i]... with
+    // site_transfer's convention sum_{ij} W[i,j] A_i (x) conj(A_j), W = P^T
+    std::vector<Cx<R>> E(1, Cx<R>(1)), N(1, Cx<R>(1));
+    for (int s = 0; s < n; ++s) {
+      const Cx<R>* P = ps[s] == 'X' ? X2 : ps[s] == 'Y' ? Y2 : ps[s] == 'Z' ? Z2 : I2;
+      const Cx<R> W[4] = {P[0], P[2], P[1], P[3]};
+      E = site_transfer(s, E, W);
+      N = site_transfer(s, N, I2);
+    }
+    const Cx<R> q = (1 / N[0].re) * E[0];
+    out[0] = (double)q.re;
+    out[1] = (double)q.im;
+  }
+
   int bond(int b) const override { return chi_[b + 1]; }
   void schmidt(int b, double* out) const override {
     for (int c = 0; c < chi_[b + 1]; ++c) out[c] = (double)L[b + 1][c];
@@ -687,6 +763,13 @@ void oracle_mps_last_diag(void* h, int* k, double* discarded, int* sweeps, int* 
   Diag d = static_cast<OracleBase*>(h)->last();
   *k = d.k; *discarded = d.discarded; *sweeps = d.sweeps; *status = d.status;
 }
+
+// One bit string per call: bits[q] for q = 0..n-1 from the uniforms u[0..n-1].
+void oracle_mps_sample(void* h, const double* u, unsigned char* bits) {
+  static_cast<OracleBase*>(h)->sample(u, bits);
+}
+// <psi|P|psi>/<psi|psi> for a string of n characters from "IXYZ".
+void oracle_mps_pauli(void* h, const char* p, double* out) { static_cast<OracleBase*>(h)->pauli(p, out); }
 
 // Stand-alone SVD of an m x n complex128 matrix T (row-major, interleaved):
 // sigma (min(m,n), unsorted, in Jacobi column order), X (m x r, column-major),

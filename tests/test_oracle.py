@@ -422,3 +422,77 @@ def test_echo_brickwork_returns_to_the_initial_state():
             sv.apply([site, site + 1], U)
     v = sv.vector()
     assert abs(abs(v[0]) - 1.0) < 1e-13 and np.max(np.abs(v[1:])) < 1e-13
+
+
+# ------------------------------------------------- sampling, Pauli strings ---
+
+PAULI = {"I": np.eye(2), "X": np.array([[0, 1], [1, 0]], dtype=complex),
+         "Y": np.array([[0, -1j], [1j, 0]]), "Z": np.diag([1.0, -1.0]).astype(complex)}
+
+
+def _brute_sample(psi, n, u):
+    """Sequential conditional sampling from the normalised |psi|^2 (the
+    marginal of the prefix over all suffixes), qubit 0 first; 0 if u < p0."""
+    w = np.abs(psi.reshape((2,) * n)) ** 2
+    bits = []
+    for s in range(n):
+        sub = w[tuple(bits)]
+        m = sub.reshape(2, -1).sum(axis=1)
+        b = 0 if u[s] < m[0] / m.sum() else 1
+        bits.append(b)
+    return np.array(bits, dtype=np.uint8)
+
+
+def _pauli_brute(psi, n, p):
+    op = np.array([[1.0]])
+    for ch in p:
+        op = np.kron(op, PAULI[ch])
+    return np.vdot(psi, op @ psi) / np.vdot(psi, psi)
+
+
+@pytest.mark.parametrize("chi_max", [64, 5])
+def test_sampling_is_sequential_conditional_sampling_of_the_stored_state(chi_max):
+    """With uniforms u the oracle's sample equals sequential sampling from the
+    brute-force distribution |<b|psi>|^2 / <psi|psi> of the stored MPS (exact,
+    or truncated and so not canonical)."""
+    rng = np.random.default_rng(500 + chi_max)
+    n = 8
+    m = oracle.OracleMPS(n, chi_max, 0.0)
+    for layer in random_layers(n, 6, rng):
+        for site, U in layer:
+            m.apply_gate(site, U)
+    psi = mps_vector(m, n)
+    u = rng.random((300, n))
+    got = m.sample(u)
+    for r in range(len(u)):
+        assert np.array_equal(got[r], _brute_sample(psi, n, u[r]))
+
+
+def test_pauli_strings_vs_statevector_and_truncated_state():
+    rng = np.random.default_rng(515)
+    n = 7
+    layers = random_layers(n, 5, rng)
+    exact, sv = run_both(n, layers)
+    trunc = oracle.OracleMPS(n, 3, 0.0)
+    for layer in layers:
+        for site, U in layer:
+            trunc.apply_gate(site, U)
+    v_t = mps_vector(trunc, n)
+    for _ in range(25):
+        p = "".join(rng.choice(list("IXYZ"), size=n))
+        assert abs(exact.pauli_expectation(p) - _pauli_brute(sv.vector(), n, p)) < 1e-13
+        assert abs(trunc.pauli_expectation(p) - _pauli_brute(v_t, n, p)) < 1e-13
+
+
+def test_pauli_strings_ghz_closed_forms():
+    n = 9
+    m = oracle.OracleMPS(n, 4, 0.0)
+    for layer in C.ghz_prefix(n):
+        for site, U in layer:
+            m.apply_gate(site, U)
+    assert abs(m.pauli_expectation("X" * n) - 1) < 1e-14
+    assert abs(m.pauli_expectation("YY" + "X" * (n - 2)) + 1) < 1e-14   # Y Y on |11> gives -1
+    assert abs(m.pauli_expectation("ZIIIIIIIZ") - 1) < 1e-14
+    assert abs(m.pauli_expectation("IIIIZIIII")) < 1e-14
+    # every string draws the GHZ pair (0...0, 1...1): a single X anywhere gives 0
+    assert abs(m.pauli_expectation("IIXIIIIII")) < 1e-14
