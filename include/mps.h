@@ -254,6 +254,26 @@ int mps_expectation(mps_handle h, int site, int k, const double* O, double* out)
  * MPS_ERR_NOMEM. Synchronises the stream. */
 int mps_reduced_density(mps_handle h, const int* qubits, int nq, double* rho);
 
+/* mps_sample - `count` bit strings drawn from |<b|psi>|^2 / <psi|psi> (the
+ * measurement of every qubit in the computational basis, Eq. 1's amplitudes)
+ * by sequential conditional sampling: qubit s of sample m is 0 when
+ * u[m n + s] < p(b_s = 0 | b_0 .. b_{s-1}), else 1. The conditional weights
+ * contract the sample's chosen prefix with right environments of the stored
+ * tensors, so they are exact for a truncated (non-canonical) state too.
+ *   u     host array of count x n uniforms in [0, 1) (the caller's random
+ *         numbers: the same u always gives the same strings)
+ *   bits  host array of count x n bytes, bits[m n + q] in {0, 1} is qubit q
+ * Errors: MPS_ERR_ARG (u outside [0, 1)), MPS_ERR_NOMEM. Synchronises the stream. */
+int mps_sample(mps_handle h, int count, const double* u, unsigned char* bits);
+
+/* mps_pauli_expectations - <psi|P|psi> / <psi|psi> for `count` Pauli strings
+ * P = P_0 (x) ... (x) P_{n-1}, each P_q one of I, X, Y, Z, by full
+ * transfer-matrix contractions of Eq. (1) (exact for the stored tensors).
+ *   paulis  host array of count x n characters from "IXYZ" (no terminators)
+ *   out     host array of count x 2 doubles (real, imaginary)
+ * Errors: MPS_ERR_ARG, MPS_ERR_NOMEM. Synchronises the stream. */
+int mps_pauli_expectations(mps_handle h, int count, const char* paulis, double* out);
+
 /* mps_get_schmidt - copies Lambda_bond (the Schmidt coefficients of the cut
  * after qubit `bond`, Eq. 2) into lambda (capacity chi_max doubles) and its
  * length into *len. Synchronises the stream. */

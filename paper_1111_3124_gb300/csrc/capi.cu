@@ -1620,6 +1620,135 @@ int rdo_impl(mps_state* h, const int* qubits, int nq, std::vector<cd>& rho) {
   return MPS_OK;
 }
 
+// --------------------------------------------------- sampling, Pauli strings ---
+
+constexpr int kSampleChunk = 4096;  // samples per pass of the sequential sampler
+
+// Bit strings by sequential conditional sampling of |<b|psi>|^2 / <psi|psi>:
+// right environments R_s of the stored tensors (built once, right to left),
+// then per site the weights of b_s = 0, 1 for every sample's chosen prefix
+// (row vectors V, GEMM-shaped over the samples), the draw against the
+// caller's uniform, and V renormalised.
+int sample_impl(mps_state* h, int count, const double* u, unsigned char* bits) {
+  int rc = flush_pending(h);
+  if (rc) return rc;
+  std::vector<int> chi;
+  if ((rc = read_chi(h, chi))) return rc;
+  const int n = h->n;
+  std::vector<size_t> env_off(n + 1);
+  size_t env_elems = 0, s_max = 1, t_max = 1;
+  int x_max = 1;
+  for (int s = 0; s <= n; ++s) {
+    env_off[s] = env_elems;
+    env_elems += (size_t)chi[s] * chi[s];
+  }
+  for (int s = 0; s < n; ++s) {
+    s_max = std::max(s_max, (size_t)2 * chi[s] * chi[s + 1]);
+    t_max = std::max(t_max, (size_t)chi[s] * chi[s + 1]);
+    x_max = std::max(x_max, chi[s + 1]);
+  }
+  const int S = std::min(count, kSampleChunk);
+  const size_t per = (size_t)S * x_max;
+  const size_t u_elems = ((size_t)S * n * sizeof(double) + sizeof(double2) - 1) / sizeof(double2);
+  const size_t b_elems = ((size_t)S * n + sizeof(double2) - 1) / sizeof(double2);
+  if ((rc = ensure_readout(h, env_elems + s_max + t_max + 5 * per + u_elems + b_elems))) return rc;
+  double2* env = h->ro_buf;
+  double2* Sc = env + env_elems;
+  double2* Tm = Sc + s_max;
+  double2* V = Tm + t_max;
+  double2* W[2] = {V + per, V + 2 * per};
+  double2* T[2] = {V + 3 * per, V + 4 * per};
+  double* d_u = reinterpret_cast<double*>(V + 5 * per);
+  unsigned char* d_bits = reinterpret_cast<unsigned char*>(V + 5 * per + u_elems);
+  // right environments: R_n = [1]; R_s = sum_i A_i R_{s+1} A_i^H, A_i = Gamma_s[i] Lambda_s
+  launch_fill_one(env + env_off[n], 1, h->stream);
+  for (int s = n - 1; s >= 0; --s) {
+    const int xl = chi[s], xr = chi[s + 1];
+    launch_scale_site(site_ptr(h, s), bond_ptr(h, s), xl, xr, h->cap, Sc, h->stream);
+    for (int i = 0; i < 2; ++i) {
+      const double2* Ai = Sc + (size_t)i * xl * xr;
+      launch_zgemm(xl, xr, xr, Ai, xr, 0, 0, env + env_off[s + 1], xr, 0, 0, 0, Tm, xr, 0, 0, 1, h->stream);
+      launch_zgemm(xl, xl, xr, Tm, xr, 0, 0, Ai, xr, 0, 1, 1, env + env_off[s], xl, 0, i, 1, h->stream);
+    }
+  }
+  for (int c0 = 0; c0 < count; c0 += S) {
+    const int m = std::min(S, count - c0);
+    CK(cudaMemcpyAsync(d_u, u + (size_t)c0 * n, sizeof(double) * m * n, cudaMemcpyHostToDevice, h->stream));
+    launch_fill_one(V, m, h->stream);  // V = [1] per sample (bond -1 has dimension 1)
+    for (int s = 0; s < n; ++s) {
+      const int xl = chi[s], xr = chi[s + 1];
+      launch_scale_site(site_ptr(h, s), bond_ptr(h, s), xl, xr, h->cap, Sc, h->stream);
+      for (int i = 0; i < 2; ++i) {
+        launch_zgemm(m, xr, xl, V, xl, 0, 0, Sc + (size_t)i * xl * xr, xr, 0, 0, 0, W[i], xr, 0, 0, 1, h->stream);
+        launch_zgemm(m, xr, xr, W[i], xr, 0, 0, env + env_off[s + 1], xr, 0, 0, 0, T[i], xr, 0, 0, 1, h->stream);
+      }
+      launch_sample_step(m, xr, W[0], W[1], T[0], T[1], d_u + s, n, d_bits + s, V, h->stream);
+    }
+    CK(cudaMemcpyAsync(bits + (size_t)c0 * n, d_bits, (size_t)m * n, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  return MPS_OK;
+}
+
+// <psi|P|psi> / <psi|psi> for Pauli strings P: transfer contractions left to
+// right with the Pauli matrix as the physical weight (and once with identities
+// for the norm).
+int pauli_impl(mps_state* h, int count, const char* ps, double* out) {
+  int rc = flush_pending(h);
+  if (rc) return rc;
+  std::vector<int> chi;
+  if ((rc = read_chi(h, chi))) return rc;
+  const int n = h->n;
+  size_t e_max = 1, s_max = 1;
+  for (int s = 0; s < n; ++s) {
+    e_max = std::max(e_max, (size_t)std::max(chi[s], chi[s + 1]) * std::max(chi[s], chi[s + 1]));
+    s_max = std::max(s_max, (size_t)2 * chi[s] * chi[s + 1]);
+  }
+  if ((rc = ensure_readout(h, 5 * e_max + s_max))) return rc;
+  double2* E0 = h->ro_buf;
+  double2* E1 = E0 + e_max;
+  double2* Tp[2] = {E1 + e_max, E1 + 2 * e_max};
+  double2* Tc = E1 + 3 * e_max;
+  double2* Sc = E1 + 4 * e_max;
+  const double2 z = make_double2(0.0, 0.0), one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0);
+  const double2 pi = make_double2(0.0, 1.0), mi = make_double2(0.0, -1.0);
+  auto contract = [&](const char* p, double2* val) -> int {
+    launch_fill_one(E0, 1, h->stream);
+    for (int s = 0; s < n; ++s) {
+      const int xl = chi[s], xr = chi[s + 1];
+      launch_scale_site(site_ptr(h, s), bond_ptr(h, s), xl, xr, h->cap, Sc, h->stream);
+      const double2* A[2] = {Sc, Sc + (size_t)xl * xr};
+      // Tp_i = A_i^T E (xr x xl)
+      for (int i = 0; i < 2; ++i) launch_zgemm(xr, xl, xl, A[i], xr, 0, 1, E0, xl, 0, 0, 0, Tp[i], xl, 0, 0, 1, h->stream);
+      // E' = sum_j (sum_i P[j][i] Tp_i) conj(A_j): ket index i, bra index j
+      const char c = p ? p[s] : 'I';
+      double2 P[2][2] = {{one, z}, {z, one}};
+      if (c == 'X') { P[0][0] = z; P[0][1] = one; P[1][0] = one; P[1][1] = z; }
+      if (c == 'Y') { P[0][0] = z; P[0][1] = mi; P[1][0] = pi; P[1][1] = z; }
+      if (c == 'Z') { P[1][1] = mone; }
+      for (int j = 0; j < 2; ++j) {
+        launch_combine2((long long)xr * xl, P[j][0], Tp[0], P[j][1], Tp[1], Tc, h->stream);
+        launch_zgemm(xr, xr, xl, Tc, xl, 0, 0, A[j], xr, 0, 1, 0, E1, xr, 0, j, 1, h->stream);
+      }
+      std::swap(E0, E1);
+    }
+    CK(cudaMemcpyAsync(val, E0, sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MPS_OK;
+  };
+  double2 norm;
+  if ((rc = contract(nullptr, &norm))) return rc;
+  for (int q = 0; q < count; ++q) {
+    double2 v;
+    if ((rc = contract(ps + (size_t)q * n, &v))) return rc;
+    out[2 * q] = v.x / norm.x;
+    out[2 * q + 1] = v.y / norm.x;
+  }
+  CK(cudaGetLastError());
+  return MPS_OK;
+}
+
 // ---------------------------------------------------------------- programs ---
 
 constexpr int kProgMaxTasks = 512;  // gate tasks per recorded pass (bounds the split-GEMM buffers)
@@ -2182,6 +2311,28 @@ int mps_expectation(mps_handle h, int site, int k, const double* O, double* out)
     for (int y = 0; y < d; ++y) acc += r[(size_t)x * d + y] * cd(O[2 * (y * d + x)], O[2 * (y * d + x) + 1]);
   out[0] = acc.real();
   out[1] = acc.imag();
+  return collect_status(h);
+}
+
+int mps_sample(mps_handle h, int count, const double* u, unsigned char* bits) {
+  if (!h || count < 0 || (count > 0 && (!u || !bits))) return fail(MPS_ERR_ARG, "bad arguments");
+  if (count == 0) return MPS_OK;
+  for (size_t e = 0; e < (size_t)count * h->n; ++e)
+    if (!(u[e] >= 0.0 && u[e] < 1.0)) return fail(MPS_ERR_ARG, "uniforms must lie in [0, 1)");
+  int rc = sample_impl(h, count, u, bits);
+  if (rc) return rc;
+  return collect_status(h);
+}
+
+int mps_pauli_expectations(mps_handle h, int count, const char* paulis, double* out) {
+  if (!h || count < 0 || (count > 0 && (!paulis || !out))) return fail(MPS_ERR_ARG, "bad arguments");
+  for (size_t e = 0; e < (size_t)count * h->n; ++e) {
+    const char c = paulis[e];
+    if (c != 'I' && c != 'X' && c != 'Y' && c != 'Z') return fail(MPS_ERR_ARG, "Pauli strings use I, X, Y, Z");
+  }
+  if (count == 0) return MPS_OK;
+  int rc = pauli_impl(h, count, paulis, out);
+  if (rc) return rc;
   return collect_status(h);
 }
 

@@ -53,6 +53,11 @@ void launch_apply1(const SiteTask* t, int ntask, int el_ub, cudaStream_t st);
 
 void launch_amplitudes(const double2* gamma, const double* lambda, const int* chi, int n, int cap,
                        const unsigned char* bits, int count, double2* out, cudaStream_t st);
+void launch_sample_step(int S, int xr, const double2* W0, const double2* W1, const double2* T0, const double2* T1,
+                        const double* u, int ustride, unsigned char* bits, double2* V, cudaStream_t st);
+void launch_combine2(long long n, double2 a0, const double2* X0, double2 a1, const double2* X1, double2* out,
+                     cudaStream_t st);
+void launch_fill_one(double2* v, int count, cudaStream_t st);
 void launch_scale_site(const double2* g, const double* lam, int xl, int xr, int cap, double2* out, cudaStream_t st);
 void launch_zgemm(int M, int N, int K, const double2* A, int lda, long long sA, int transA, const double2* B,
                   int ldb, long long sB, int conjB, int transB, double2* C, int ldc, long long sC, int accumulate,

@@ -95,6 +95,65 @@ __global__ void __launch_bounds__(256) k_zgemm(int M, int N, int K, const double
   }
 }
 
+// Sequential sampling, one step (one warp per sample m): the weights of
+// b_s = 0 and 1, p_i = <W_i R W_i^H> with W_i = V A_i (row m of W_i, T_i =
+// W_i R), b = 0 when u < p_0 / (p_0 + p_1), then V <- W_b / sqrt(p_b).
+__global__ void k_sample_step(int S, int xr, const double2* W0, const double2* W1, const double2* T0,
+                              const double2* T1, const double* u, int ustride, unsigned char* bits, double2* V) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= S) return;
+  const size_t row = (size_t)warp * xr;
+  double p0 = 0.0, p1 = 0.0;
+  for (int c = lane; c < xr; c += 32) {
+    const double2 w0 = W0[row + c], t0 = T0[row + c], w1 = W1[row + c], t1 = T1[row + c];
+    p0 = fma(t0.x, w0.x, fma(t0.y, w0.y, p0));  // Re(t conj(w))
+    p1 = fma(t1.x, w1.x, fma(t1.y, w1.y, p1));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+    p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+  }
+  const int b = u[(size_t)warp * ustride] < p0 / (p0 + p1) ? 0 : 1;
+  if (lane == 0) bits[(size_t)warp * ustride] = (unsigned char)b;
+  const double pb = b ? p1 : p0;
+  const double inv = pb > 0.0 ? 1.0 / sqrt(pb) : 0.0;
+  const double2* Wb = b ? W1 : W0;
+  for (int c = lane; c < xr; c += 32) {
+    const double2 w = Wb[row + c];
+    V[row + c] = make_double2(inv * w.x, inv * w.y);
+  }
+}
+
+// out = a0 X0 + a1 X1 (complex coefficients), element-wise
+__global__ void k_combine2(long long n, double2 a0, const double2* X0, double2 a1, const double2* X1, double2* out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double2 x = X0[e], y = X1[e];
+    out[e] = make_double2(a0.x * x.x - a0.y * x.y + a1.x * y.x - a1.y * y.y,
+                          a0.x * x.y + a0.y * x.x + a1.x * y.y + a1.y * y.x);
+  }
+}
+
+__global__ void k_fill_one(double2* v, int count) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) v[e] = make_double2(1.0, 0.0);
+}
+
+void launch_sample_step(int S, int xr, const double2* W0, const double2* W1, const double2* T0, const double2* T1,
+                        const double* u, int ustride, unsigned char* bits, double2* V, cudaStream_t st) {
+  k_sample_step<<<(S * 32 + 255) / 256, 256, 0, st>>>(S, xr, W0, W1, T0, T1, u, ustride, bits, V);
+}
+
+void launch_combine2(long long n, double2 a0, const double2* X0, double2 a1, const double2* X1, double2* out,
+                     cudaStream_t st) {
+  long long b = (n + 255) / 256;
+  if (b > 4096) b = 4096;
+  k_combine2<<<(int)(b < 1 ? 1 : b), 256, 0, st>>>(n, a0, X0, a1, X1, out);
+}
+
+void launch_fill_one(double2* v, int count, cudaStream_t st) {
+  k_fill_one<<<(count + 255) / 256, 256, 0, st>>>(v, count);
+}
+
 void launch_amplitudes(const double2* gamma, const double* lambda, const int* chi, int n, int cap,
                        const unsigned char* bits, int count, double2* out, cudaStream_t st) {
   k_amplitudes<<<count, 256, 2 * cap * sizeof(double2), st>>>(gamma, lambda, chi, n, cap, bits, out);

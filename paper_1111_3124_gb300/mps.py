@@ -37,6 +37,7 @@ EXPORTS = [
     "mps_mlp_create", "mps_mlp_destroy", "mps_mlp_params", "mps_mlp_forward", "mps_mlp_loss_grad", "mps_mlp_train",
     "mps_layer_features", "mps_set_predictor", "mps_sketch_stats", "mps_set_limits", "mps_debug_fail_alloc",
     "mps_program_create", "mps_program_run", "mps_program_updates", "mps_program_destroy", "mps_set_tuning",
+    "mps_sample", "mps_pauli_expectations",
 ]
 
 
@@ -98,6 +99,8 @@ def load_library(path: str = LIB_PATH):
                              ctypes.POINTER(ctypes.c_longlong)],
         "mps_set_limits": [P, I],
         "mps_set_tuning": [P, I, ip, ip, ip],
+        "mps_sample": [P, I, dp, P],
+        "mps_pauli_expectations": [P, I, bp, dp],
         "mps_program_create": [I, ctypes.POINTER(P), I, ip, ip, ip, ip, P, ctypes.POINTER(P)],
         "mps_program_run": [P],
         "mps_program_updates": [P, ctypes.POINTER(ctypes.c_longlong)],
@@ -252,6 +255,22 @@ class MPS:
         out = np.zeros(2)
         check(load_library().mps_expectation(self._h, site, k, _dp(O.view(np.float64)), _dp(out)))
         return complex(out[0], out[1])
+
+    def sample(self, u) -> np.ndarray:
+        """Bit strings (rows, qubit 0 first) from uniforms u (rows of n values in [0, 1))."""
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1, self.n))
+        bits = np.zeros(u.shape, dtype=np.uint8)
+        check(load_library().mps_sample(self._h, u.shape[0], _dp(u), ctypes.c_void_p(bits.ctypes.data)))
+        return bits
+
+    def pauli_expectations(self, strings) -> np.ndarray:
+        """<P> for Pauli strings (each of length n over "IXYZ")."""
+        strings = list(strings)
+        assert all(len(p) == self.n for p in strings)
+        buf = "".join(strings).encode()
+        out = np.zeros((len(strings), 2))
+        check(load_library().mps_pauli_expectations(self._h, len(strings), buf, _dp(out)))
+        return out[:, 0] + 1j * out[:, 1]
 
     def reduced_density(self, qubits) -> np.ndarray:
         q = np.ascontiguousarray(np.asarray(qubits, dtype=np.int32))
