@@ -383,6 +383,41 @@ def run_config4(prec, count: int, steps: int, tune_table=()):
     return out
 
 
+def run_routing(prec, tune_table=()):
+    """Gates on non-neighbours (Sec. 3.2's applyU on qubits 0 and 2): distance-2
+    Haar U(4) gates on a chi_max = 64 state of 32 qubits, routed as one U(8)
+    update each, or as SWAP, gate, SWAP (three two-site updates each)."""
+    import torch
+    from paper_1111_3124_gb300 import circuits as C
+    from paper_1111_3124_gb300.mps import MPS
+    n, chi = 32, 64
+    rng = np.random.default_rng(C.SEED_BASE + 31)
+    base = C.brickwork(n, 6, rng)
+    gates = [((4 * j, 4 * j + 2), C.haar_unitary(4, rng)) for j in range(n // 4)]
+    gates += [((4 * j + 3, 4 * j + 1), C.haar_unitary(4, rng)) for j in range(n // 4)]
+    out, amps = {}, {}
+    bits = np.random.default_rng(7).integers(0, 2, size=(64, n)).astype(np.uint8)
+    for route in ("embed", "swap"):
+        m = MPS(n, chi, 1e-12, prec)
+        m.set_tuning(list(tune_table))
+        m.run_layers(base)
+        m.sync()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for (q, U) in gates:
+            m.apply_gate_on(list(q), U, route=route)
+        m.sync()
+        dt = time.perf_counter() - t0
+        amps[route] = m.amplitudes(bits)
+        out[route] = {"seconds": dt, "gates": len(gates), "gates_per_s": len(gates) / dt,
+                      "updates": len(gates) * (1 if route == "embed" else 3),
+                      "update_kind": "three-site" if route == "embed" else "two-site"}
+        m.close()
+    out["max_amp_diff_between_routes"] = float(np.max(np.abs(amps["embed"] - amps["swap"])))
+    out["workload"] = "n=32, chi_max=64 after 6 brickwork layers; 16 distance-2 Haar U(4) gates"
+    return out
+
+
 def run_gpu(a):
     import torch
     import torch.distributed as dist
@@ -608,6 +643,7 @@ def run_gpu(a):
         if not a.no_extra_configs:
             line["three_site"] = run_config3(prec, 2, tune_table)
             line["many_circuits"] = run_config4(prec, a.batch_circuits, 1, tune_table)
+            line["routing"] = run_routing(prec, tune_table)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if prog is not None:

@@ -166,6 +166,18 @@ int mps_reset(mps_handle h);
  * Errors: MPS_ERR_ARG (k, site range, NULL), MPS_ERR_NOT_UNITARY. */
 int mps_apply_gate(mps_handle h, int site, int k, const double* U);
 
+/* mps_apply_gate_on - Sec. 3.2 ("applyU(U, q0, q1)", e.g. CNOT on qubits 0
+ * and 2): a one- or two-qubit gate on any listed qubits. The first listed
+ * qubit is the most significant bit of U's index, whatever the qubits' order.
+ * Neighbours are one two-site update. At distance 2, route 0 embeds U as a
+ * U(8) on (q, q+1, q+2) with the identity on the middle qubit (one three-site
+ * update); otherwise SWAP updates carry the higher qubit next to the lower
+ * one, U acts there, and SWAP updates carry it back (2 (d - 1) + 1 two-site
+ * updates for distance d, each truncated as usual). route: 0 (embed at
+ * distance 2, SWAPs beyond) or 1 (SWAPs always).
+ * Errors: MPS_ERR_ARG, MPS_ERR_NOT_UNITARY. */
+int mps_apply_gate_on(mps_handle h, int nq, const int* qubits, const double* U, int route);
+
 /* mps_apply_layer - n_gates gates of the same size k on pairwise disjoint
  * qubit ranges, updated together in one batched pass (the gates of one
  * circuit layer commute, so the result equals applying them in any order).

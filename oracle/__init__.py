@@ -111,14 +111,35 @@ class OracleMPS:
         if rc != 0:
             raise RuntimeError("oracle gate failed: %d" % rc)
 
-    def apply_gate_on(self, qubits, U) -> None:
+    def apply_gate_on(self, qubits, U, route: str = "embed") -> None:
         """Gate on listed qubits (first = most significant). Adjacent increasing
         qubits go straight through; a two-qubit gate on (q, q+2) is embedded as
-        an 8x8 gate on (q, q+1, q+2) with the identity on q+1."""
+        an 8x8 gate on (q, q+1, q+2) with the identity on q+1 (route "embed");
+        otherwise SWAP gates carry the higher qubit next to the lower one and
+        back (route "swap", and every distance above 2)."""
         U = _c128(U)
         qubits = list(qubits)
         if len(qubits) == 1 or all(qubits[t + 1] == qubits[t] + 1 for t in range(len(qubits) - 1)):
             self.apply_gate(qubits[0], U)
+            return
+        if len(qubits) == 2 and (abs(qubits[1] - qubits[0]) > 2 or route == "swap" or qubits[1] == qubits[0] - 1):
+            q0, q1 = qubits
+            if q0 > q1:  # index bits in increasing qubit order
+                P = np.zeros((4, 4))
+                for a in range(2):
+                    for b in range(2):
+                        P[b * 2 + a, a * 2 + b] = 1
+                U = P @ U @ P.T
+                q0, q1 = q1, q0
+            S = np.zeros((4, 4))
+            for a in range(2):
+                for b in range(2):
+                    S[b * 2 + a, a * 2 + b] = 1
+            for t in range(q1 - 1, q0, -1):
+                self.apply_gate(t, S)
+            self.apply_gate(q0, U)
+            for t in range(q0 + 1, q1):
+                self.apply_gate(t, S)
             return
         if len(qubits) == 2 and abs(qubits[1] - qubits[0]) == 2:
             q0, q1 = qubits

@@ -2201,6 +2201,55 @@ int mps_layer_features(mps_handle h, int k, int n_gates, const int* sites, const
   return e == cudaSuccess ? MPS_OK : fail(MPS_ERR_CUDA, "features");
 }
 
+int mps_apply_gate_on(mps_handle h, int nq, const int* qubits, const double* U, int route) {
+  if (!h || !qubits || !U) return fail(MPS_ERR_ARG, "bad arguments");
+  if (nq < 1 || nq > 2) return fail(MPS_ERR_ARG, "nq must be 1 or 2");
+  if (route != 0 && route != 1) return fail(MPS_ERR_ARG, "route must be 0 or 1");
+  for (int t = 0; t < nq; ++t)
+    if (qubits[t] < 0 || qubits[t] >= h->n) return fail(MPS_ERR_ARG, "qubit out of range");
+  if (nq == 1) return apply_layer_impl(h, 1, 1, qubits, U);
+  const int a = qubits[0], b = qubits[1];
+  if (a == b) return fail(MPS_ERR_ARG, "the two qubits must differ");
+  if (!is_unitary(U, 4)) return fail(MPS_ERR_NOT_UNITARY, "gate is not unitary");
+  // the gate with its index bits in increasing qubit order: V = S U S when
+  // the first listed qubit is the higher one (S swaps the two index bits)
+  double V[32];
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) {
+      const int rr = a < b ? r : ((r & 1) << 1 | r >> 1), cc = a < b ? c : ((c & 1) << 1 | c >> 1);
+      V[2 * (r * 4 + c)] = U[2 * (rr * 4 + cc)];
+      V[2 * (r * 4 + c) + 1] = U[2 * (rr * 4 + cc) + 1];
+    }
+  const int lo = std::min(a, b), hi = std::max(a, b), d = hi - lo;
+  if (d == 1) return apply_layer_impl(h, 2, 1, &lo, V);
+  if (d == 2 && route == 0) {
+    // U(8) on (lo, lo+1, lo+2) with the identity on the middle qubit
+    double W[128];
+    std::memset(W, 0, sizeof(W));
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 2; ++k)
+          for (int l = 0; l < 2; ++l)
+            for (int m = 0; m < 2; ++m) {
+              const int r = i * 4 + m * 2 + j, c = k * 4 + m * 2 + l, src = (i * 2 + j) * 4 + (k * 2 + l);
+              W[2 * (r * 8 + c)] = V[2 * src];
+              W[2 * (r * 8 + c) + 1] = V[2 * src + 1];
+            }
+    return apply_layer_impl(h, 3, 1, &lo, W);
+  }
+  // SWAP updates carry qubit hi down to lo+1, the gate acts there, and SWAPs
+  // carry it back (each SWAP is a two-site update with its own truncation)
+  static const double S[32] = {1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0,
+                               0, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0};
+  int rc;
+  for (int t = hi - 1; t > lo; --t)
+    if ((rc = apply_layer_impl(h, 2, 1, &t, S))) return rc;
+  if ((rc = apply_layer_impl(h, 2, 1, &lo, V))) return rc;
+  for (int t = lo + 1; t < hi; ++t)
+    if ((rc = apply_layer_impl(h, 2, 1, &t, S))) return rc;
+  return MPS_OK;
+}
+
 int mps_set_predictor(mps_handle h, mps_mlp_handle m) {
   if (!h) return fail(MPS_ERR_ARG, "NULL handle");
   h->predictor = m;

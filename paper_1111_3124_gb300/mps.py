@@ -37,7 +37,7 @@ EXPORTS = [
     "mps_mlp_create", "mps_mlp_destroy", "mps_mlp_params", "mps_mlp_forward", "mps_mlp_loss_grad", "mps_mlp_train",
     "mps_layer_features", "mps_set_predictor", "mps_sketch_stats", "mps_set_limits", "mps_debug_fail_alloc",
     "mps_program_create", "mps_program_run", "mps_program_updates", "mps_program_destroy", "mps_set_tuning",
-    "mps_sample", "mps_pauli_expectations",
+    "mps_sample", "mps_pauli_expectations", "mps_apply_gate_on",
 ]
 
 
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH):
         "mps_set_limits": [P, I],
         "mps_set_tuning": [P, I, ip, ip, ip],
         "mps_sample": [P, I, dp, P],
+        "mps_apply_gate_on": [P, I, ip, dp, I],
         "mps_pauli_expectations": [P, I, bp, dp],
         "mps_program_create": [I, ctypes.POINTER(P), I, ip, ip, ip, ip, P, ctypes.POINTER(P)],
         "mps_program_run": [P],
@@ -222,23 +223,15 @@ class MPS:
                                               ctypes.byref(fl), ctypes.byref(na)))
         return {"ms": ms.value, "launches": nl.value, "flops": fl.value, "launches_all": na.value}
 
-    def apply_gate_on(self, qubits, U) -> None:
-        """Gate on listed qubits (first = most significant index bit): adjacent
-        increasing qubits directly; a two-qubit gate on (q, q+-2) as a U(8) on
-        (q, q+1, q+2) with the identity on the middle qubit."""
+    def apply_gate_on(self, qubits, U, route: str = "embed") -> None:
+        """Gate on listed qubits (first = most significant index bit), routed by
+        the library (mps_apply_gate_on): neighbours directly; distance 2 as a
+        U(8) with the identity on the middle qubit (route "embed") or by SWAP
+        updates (route "swap"); farther by SWAP updates."""
         U = _c128(U)
-        q = list(qubits)
-        if len(q) == 1 or all(q[t + 1] == q[t] + 1 for t in range(len(q) - 1)):
-            self.apply_gate(q[0], U)
-            return
-        if len(q) == 2 and abs(q[1] - q[0]) == 2:
-            T = U.reshape(2, 2, 2, 2)
-            if q[0] > q[1]:
-                T = T.transpose(1, 0, 3, 2)
-            U8 = np.einsum("ijkl,mn->imjknl", T, np.eye(2)).reshape(8, 8)
-            self.apply_gate(min(q), U8)
-            return
-        raise NotImplementedError("only adjacent gates and distance-2 two-qubit gates")
+        q = np.ascontiguousarray(np.asarray(qubits, dtype=np.int32))
+        check(load_library().mps_apply_gate_on(self._h, len(q), _ip(q), _dp(U.view(np.float64)),
+                                               0 if route == "embed" else 1))
 
     def amplitudes(self, bits) -> np.ndarray:
         b = np.ascontiguousarray(np.asarray(bits, dtype=np.uint8).reshape(-1, self.n))

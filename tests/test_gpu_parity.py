@@ -272,3 +272,35 @@ def test_single_three_site_update_chi128_config3_shape():
         assert spectrum_err(gl[b], rl[b]) < SPEC_TOL
     tg, tr = three_site_tensor(gg, gl, 1), three_site_tensor(rg, rl, 1)
     assert np.max(np.abs(tg - tr)) < 1e-11 * np.max(np.abs(tr))
+
+
+@pytest.mark.parametrize("route", ["embed", "swap"])
+def test_non_adjacent_gates_vs_statevector_and_oracle(route):
+    """mps_apply_gate_on: every order and distance of the two qubits, exact
+    (vs the state vector) and truncating (vs the oracle's same routing)."""
+    rng = np.random.default_rng(4500)
+    pairs = [(0, 2), (5, 3), (1, 6), (7, 0), (4, 3), (2, 7), (3, 5)]
+    n = 8
+    g = gpu_mps(n, 16, 0.0)
+    sv = StateVector(n)
+    for (a, b) in pairs:
+        U = C.haar_unitary(4, rng)
+        g.apply_gate_on([a, b], U, route=route)
+        sv.apply([a, b], U)
+    np.testing.assert_allclose(g.amplitudes(all_bits(n)), sv.vector(), atol=AMP_TOL)
+    # truncating: n = 12, chi_max = 6
+    n = 12
+    g = gpu_mps(n, 6, 1e-12)
+    o = oracle.OracleMPS(n, 6, 1e-12)
+    for layer in C.brickwork(n, 3, rng):
+        for site, U in layer:
+            g.apply_gate(site, U)
+            o.apply_gate(site, U)
+    for (a, b) in [(0, 4), (9, 2), (5, 7), (11, 6)]:
+        U = C.haar_unitary(4, rng)
+        g.apply_gate_on([a, b], U, route=route)
+        o.apply_gate_on([a, b], U, route=route)
+    bits = np.random.default_rng(1).integers(0, 2, size=(64, n)).astype(np.uint8)
+    np.testing.assert_allclose(g.amplitudes(bits), [o.amplitude(b) for b in bits], atol=AMP_TOL)
+    for b in range(n - 1):
+        assert spectrum_err(g.schmidt(b), o.schmidt(b)) < SPEC_TOL

@@ -496,3 +496,18 @@ def test_pauli_strings_ghz_closed_forms():
     assert abs(m.pauli_expectation("IIIIZIIII")) < 1e-14
     # every string draws the GHZ pair (0...0, 1...1): a single X anywhere gives 0
     assert abs(m.pauli_expectation("IIXIIIIII")) < 1e-14
+
+
+@pytest.mark.parametrize("route", ["embed", "swap"])
+def test_non_adjacent_gates_by_routing_vs_statevector(route):
+    """Sec. 3.2 applies two-qubit gates to non-neighbours: the oracle's routes
+    (U(8) embedding at distance 2, SWAP chains) reproduce the state vector for
+    every order and distance of the two qubits."""
+    rng = np.random.default_rng(4400)
+    n = 8
+    m, sv = run_both(n, random_layers(n, 3, rng, ks=(2,)))
+    for (a, b) in [(0, 2), (5, 3), (1, 6), (7, 0), (4, 3), (2, 7)]:
+        U = C.haar_unitary(4, rng)
+        m.apply_gate_on([a, b], U, route=route)
+        sv.apply([a, b], U)
+    np.testing.assert_allclose(mps_vector(m, n), sv.vector(), atol=1e-13)
