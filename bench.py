@@ -43,10 +43,37 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 KERNEL_CLASSES = ["jacobi_f64", "theta_contract_f64", "truncate_rewrite", "split_gemm_tc", "jacobi_f32", "split_aux"]
 
 
+def measure_alu_peaks():
+    """fp32 and binary64 throughput of the library GEMM (torch.matmul on the
+    CUDA cores, tf32 off), best of three at 8192^3 / 4096^3: the measured ALU
+    peaks the Jacobi kernels are held against."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out = {}
+    for name, dt, n in (("fp32", torch.float32, 8192), ("fp64", torch.float64, 4096)):
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        torch.matmul(a, b)
+        best = float("inf")
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        out[name + "_tflops"] = 2.0 * n ** 3 / best / 1e12
+        del a, b
+    out["how"] = "torch.matmul fp32 8192^3 and fp64 4096^3 (tf32 off), best of 3, CUDA events"
+    return out
+
+
 def peaks():
     """Roofline denominators. Tensor: MEASURED_PEAKS.json (bf16, sustained for a
     kernel timed inside a long step). ALU: GB300 unit counts x max SM clock
-    (152 SMs, 2070 MHz; binary64 2 FMA/clk/SM, fp32 128 FMA/clk/SM)."""
+    (152 SMs, 2070 MHz; binary64 2 FMA/clk/SM, fp32 128 FMA/clk/SM), replaced
+    by the measured GEMM throughput when the bench has measured it."""
     try:
         mp = json.load(open(PEAKS))
     except (OSError, ValueError):
@@ -574,13 +601,14 @@ def run_gpu(a):
     e2e_value = job_throughput(nup, world, t_e2e)
 
     pk = peaks()
+    alu = measure_alu_peaks()
     roof_def = {  # class -> (kernel, bound, peak TFLOP/s, peak source)
-        0: ("k_jacobi_pair<8,double> (blocked one-sided Jacobi, binary64)", "alu", pk["fp64_tflops"],
-            "binary64 ALU: 152 SMs x 2 FMA/clk x max SM clock"),
-        1: ("k_contract (theta, binary64)", "alu", pk["fp64_tflops"], "binary64 ALU: unit counts x clock"),
+        0: ("k_jacobi_pair<8,double> (blocked one-sided Jacobi, binary64)", "alu", alu["fp64_tflops"],
+            "measured binary64 GEMM throughput (" + alu["how"] + ")"),
+        1: ("k_contract (theta, binary64)", "alu", alu["fp64_tflops"], "measured binary64 GEMM throughput"),
         3: ("k_oz_gemm (split-precision bf16 tcgen05 GEMM)", "tensor", pk["bf16_tflops"], pk["bf16_source"]),
-        4: ("k_jacobi_pair_f32<16> (fp32 preconditioning sweeps)", "alu", pk["fp32_tflops"],
-            "fp32 ALU: 152 SMs x 128 FMA/clk x max SM clock"),
+        4: ("k_jacobi_pair_f32<16> (fp32 preconditioning sweeps)", "alu", alu["fp32_tflops"],
+            "measured fp32 GEMM throughput (" + alu["how"] + ")"),
     }
     dom = max(roof_def, key=lambda i: prof[i]["ms"])
     d = prof[dom]
@@ -619,6 +647,8 @@ def run_gpu(a):
                                   "source": tune_source},
                        "max_bond": int(max(chi)) if len(chi) else 1},
             "roofline": roof, "kernels": kernels, "clocks": clocks,
+            "alu_peaks": {"measured": alu, "from_unit_counts": {"fp32_tflops": pk["fp32_tflops"],
+                                                                 "fp64_tflops": pk["fp64_tflops"]}},
             "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "path": "mps_apply_layer with host gates (eager), D2H of the middle bond's Lambda"},
             "gpu_launches": int(prof[0]["launches_all"])}
