@@ -155,14 +155,17 @@ def routing_quality(predictor, n, layers, chi_max, cutoff, prec: int = PREC_FP64
 
 
 def deploy(predictor, n: int = 96, depth: int = 30, chi_max: int = 512, cutoff: float = 1e-10, prec: int = 1,
-           seed: int = 0):
-    """The deployment workload (Haar U(4) brickwork, predictor-sized sketch
-    with the full Jacobi SVD as fallback) against the full SVD on the same
-    circuit: wall times, the gain, the sketch statistics, and the largest
-    Schmidt-value and amplitude differences between the two runs."""
+           seed: int = 0, kind: str = "haar"):
+    """The deployment workload (Haar U(4) brickwork, or with kind "weak" a
+    brickwork of weakly entangling gates exp(-it(XX+YY+ZZ)), t <= 0.15,
+    dressed with Haar single-qubit gates; predictor-sized sketch with the full
+    Jacobi SVD as fallback) against the full SVD on the same circuit: wall
+    times, the gain, the sketch statistics, and the largest Schmidt-value and
+    amplitude differences between the two runs."""
     import time
     import torch
-    layers = C.brickwork(n, depth, np.random.default_rng(C.SEED_BASE + 5000 + seed))
+    rng = np.random.default_rng(C.SEED_BASE + 5000 + seed)
+    layers = C.brickwork(n, depth, rng) if kind == "haar" else C.weak_brickwork(n, depth, rng, t_max=0.15)
     out = {}
     runs = {}
     for name, pred in (("full", None), ("predictor", predictor)):
@@ -201,12 +204,18 @@ def main() -> None:
     ap.add_argument("--out", default=None)
     ap.add_argument("--deploy", action="store_true")
     ap.add_argument("--deploy-depth", type=int, default=30)
+    ap.add_argument("--mix", type=int, default=0,
+                    help="also train on this many mixed circuits (Haar, weak, echo; chi <= 128)")
+    ap.add_argument("--deploy-weak", action="store_true")
     a = ap.parse_args()
     from . import build as B
     B.build()
     t0 = time.perf_counter()
     X, T = config2_training_set(a.circuits, seed=1)
     Xv, Tv = config2_training_set(a.heldout, seed=2)
+    if a.mix:
+        Xm, Tm = training_set(seed=3, circuits=a.mix)
+        X, T = np.concatenate([X, Xm]), np.concatenate([T, Tm])
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
     p = train(X, T, seed=0, epochs=a.epochs, batch=512, lr=2e-3)
@@ -217,6 +226,8 @@ def main() -> None:
         np.save(a.out, p.params)
     if a.deploy:
         rep["deploy"] = deploy(p, depth=a.deploy_depth)
+    if a.deploy_weak:
+        rep["deploy_weak"] = deploy(p, depth=a.deploy_depth, kind="weak")
     print(json.dumps(rep))
 
 

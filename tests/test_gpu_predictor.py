@@ -7,7 +7,9 @@ capture (singular values above cutoff/100) is close to theta's smaller
 dimension, so the predictor routes nearly every update to the full SVD: the
 gain measured is about 1 (the predictor's cost against the sketches it
 avoids). Every update is either sketched or routed; the results of both
-runs agree within the binary64 tolerances; the timings are printed."""
+runs agree within the binary64 tolerances; the predictor's overhead stays
+bounded (gain above 0.8); the updates it routes to the full SVD are ones a
+sketch could not have taken; the timings are printed."""
 import time
 
 import numpy as np
@@ -68,3 +70,19 @@ def test_gain_of_the_trained_predictor(trained, kind):
     assert np.max(np.abs(skt.amplitudes(bits) - full.amplitudes(bits))) < 1e-10
     assert st["sketched"] + st["routed_full"] == C.count_updates(layers)
     assert st["accepted"] <= st["sketched"]
+    assert t_full / t_skt > 0.8, (t_full, t_skt)
+
+
+def test_routing_quality_on_haar(trained):
+    """Replayed on a full-SVD run (every update's true sketch rank known):
+    what the predictor sends to the full SVD needed it, and what it would
+    sketch would be accepted."""
+    P, p, _, _ = trained
+    n, chi, cutoff, depth = 24, 128, 1e-10, 14
+    layers = C.brickwork(n, depth, np.random.default_rng(77))
+    q = P.routing_quality(p, n, layers, chi, cutoff)
+    print("routing quality:", q)
+    assert q["sketched"] + q["routed_full"] == C.count_updates(layers)
+    assert q["routed_full"] > 0 and q["full_needed"] >= 0.9, q
+    if q["sketched"]:
+        assert q["sketch_would_accept"] >= 0.8, q
