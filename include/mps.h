@@ -432,6 +432,113 @@ int mps_gate2_update_noalloc(double* d_gamma_l, double* d_gamma_r, const double*
 int mps_split_zgemm(int M, int N, int K, const double* dA, long long lda, const double* dB, long long ldb,
                     double* dC, long long ldc, int slices, void* stream);
 
+/* ---- Beyond binary64: double-word MPS for small bond dimensions ----------
+ * The paper runs the whole simulation in MPFR multiprecision (Sec. 1; the
+ * Sec. 3.2 example sets 256 bits) so that the Schmidt spectra of Eq. (2),
+ * which span many orders of magnitude, keep their small values. This
+ * separate handle keeps the Vidal form of Eq. (1) in double-word arithmetic
+ * (a value is the unevaluated sum hi + lo of two doubles, about 106
+ * significant bits) and runs every step of the Sec. 3.1 update in it:
+ * theta, the one-sided Jacobi SVD, truncation, renormalisation and the
+ * Lambda^-1 rewrite. Bond dimensions up to 32; one- and two-qubit gates.
+ * Truncation keeps sigma_j > max(cutoff, Mw 2^-104) ||sigma||, at most
+ * chi_max values, at least one (Mw: rows of the Jacobi working matrix).
+ * Calls on one handle run in order on its stream; errors found on the device
+ * (MPS_ERR_NOCONVERGE) are reported by the next synchronising call, and the
+ * gate that failed leaves its tensors unchanged. */
+typedef struct mps_dd_state* mps_dd_handle;
+
+/* n >= 2 qubits in |0...0>; 1 <= chi_max <= 32 (MPS_ERR_TOO_LARGE above);
+ * 0 <= cutoff < 1. Errors: MPS_ERR_ARG, MPS_ERR_TOO_LARGE, MPS_ERR_NOMEM,
+ * MPS_ERR_CUDA. */
+int mps_dd_create(int n, int chi_max, double cutoff, mps_dd_handle* out);
+int mps_dd_destroy(mps_dd_handle h);
+/* Back to |0...0>, counters cleared. */
+int mps_dd_reset(mps_dd_handle h);
+/* Runs the handle's work on `stream` (cudaStream_t; NULL = legacy default). */
+int mps_dd_set_stream(mps_dd_handle h, void* stream);
+/* Sweep limit of one SVD, 1..60 (default 60). */
+int mps_dd_set_limits(mps_dd_handle h, int max_sweeps);
+
+/* mps_dd_apply_layer - n_gates gates on disjoint qubits, k = 1 (U(2) on
+ * sites[g]) or k = 2 (U(4) on sites[g], sites[g]+1), Sec. 3.1. U_hi holds
+ * the gates as complex128 2^k x 2^k row-major matrices, gate after gate (host
+ * pointer); U_lo (host, same layout, may be NULL) holds low parts, each gate
+ * entry being hi + lo exactly. Both are copied before the call returns; the
+ * update runs asynchronously. Errors: MPS_ERR_ARG (k, range, overlap),
+ * MPS_ERR_CUDA. */
+int mps_dd_apply_layer(mps_dd_handle h, int k, int n_gates, const int* sites, const double* U_hi,
+                       const double* U_lo);
+/* The same with the layer already in device memory: d_sites (n_gates ints),
+ * d_U_hi / d_U_lo (as above, d_U_lo may be NULL) are read by the kernels when
+ * they run, so they must stay valid until the handle's stream has passed
+ * them. `sites` (host copy of d_sites) is used to check the layer. */
+int mps_dd_apply_layer_device(mps_dd_handle h, int k, int n_gates, const int* sites, const int* d_sites,
+                              const double* d_U_hi, const double* d_U_lo);
+/* Waits for the handle's stream; reports a deferred device error, clearing it. */
+int mps_dd_sync(mps_dd_handle h);
+/* n+1 bond dimensions (chi[0] = chi[n] = 1). Synchronises. */
+int mps_dd_bond_dims(mps_dd_handle h, int* chi);
+/* Lambda_bond (Eq. 2), descending: hi and lo parts (either may be NULL),
+ * *len values (at most chi_max). Synchronises. */
+int mps_dd_get_schmidt(mps_dd_handle h, int bond, double* hi, double* lo, int* len);
+/* <b|psi> of Eq. (1) for `count` bit strings (bits[count][n], one byte per
+ * qubit, 0/1): out[count][4] = (re hi, re lo, im hi, im lo). Synchronises.
+ * Errors: MPS_ERR_ARG, MPS_ERR_NOMEM, MPS_ERR_CUDA. */
+int mps_dd_amplitudes(mps_dd_handle h, int count, const unsigned char* bits, double* out);
+/* Two-site updates issued since create/reset, Jacobi sweeps they ran, and
+ * the binary64 operations the theta and Jacobi kernels executed (counted on
+ * the device). Synchronises. Any output may be NULL. */
+int mps_dd_stats(mps_dd_handle h, long long* updates, long long* sweeps, double* flops);
+
+/* ---- Hermitian matrices: the library's second workload --------------------
+ * Sec. 2 lists the diagonalisation of a Hermitian matrix among the matrix
+ * library's functions, and its NMR example (Sec. 2.1) builds a thermal state
+ * with exp_H(-(h / k_B T) H), normalises it by its trace, tilts a spin with a
+ * pulse, records <X> of that spin under H at intervals dt, zero-pads the
+ * record and takes the modulus of its DFT. These calls do each step on the
+ * GPU for `count` independent problems at once. Matrices are D x D
+ * complex128, row-major, one after another in DEVICE memory; 1 <= D <= 64
+ * (MPS_ERR_TOO_LARGE above). Every call synchronises `stream` (cudaStream_t,
+ * NULL = legacy default) and allocates its scratch with cudaMalloc.
+ * Errors: MPS_ERR_ARG, MPS_ERR_TOO_LARGE, MPS_ERR_NOMEM, MPS_ERR_CUDA,
+ * MPS_ERR_NOCONVERGE (a Jacobi sweep limit of 60 was hit). */
+
+/* Eigenvalues in ascending order d_w[count][D] and eigenvectors
+ * d_V[count][D][D] (complex128, column k of problem b is the eigenvector of
+ * d_w[b][k]) of Hermitian d_H (only the Hermitian part is meaningful: the
+ * diagonal's imaginary parts are ignored). Cyclic two-sided Jacobi; a pair is
+ * rotated while |h_pq| > D 2^-53 ||H||_F. */
+int mps_heev_batched(int count, int D, const double* d_H, double* d_w, double* d_V, void* stream);
+
+/* kind 0: d_out = exp(a H) for the complex scalar a = a_re + i a_im (exp_H of
+ * Sec. 2.1; a = -i t gives the propagator exp(-i H t)).
+ * kind 1: d_out = exp(-beta H) / Tr exp(-beta H) with beta = a_re (the
+ * thermal state), computed in H's eigenbasis with the weights shifted so that
+ * the largest is 1. */
+int mps_hermitian_function_batched(int count, int D, const double* d_H, int kind, double a_re, double a_im,
+                                   double* d_out, void* stream);
+
+/* Free-induction decay: with rho' = P rho P^H (d_P NULL: rho' = rho),
+ * d_signal[b][m] = Tr(exp(-i H t_m) rho' exp(i H t_m) O), t_m = m dt,
+ * m = 0..N-1 (complex128), evaluated in H's eigenbasis as
+ * sum_jk rho~_jk O~_kj exp(-i (lambda_j - lambda_k) t_m) with each phase
+ * computed directly from t_m. count <= 65535. */
+int mps_fid_batched(int count, int D, const double* d_rho, const double* d_H, const double* d_O, const double* d_P,
+                    double dt, int N, double* d_signal, void* stream);
+
+/* Statistics of the last Jacobi diagonalisation run on the calling thread
+ * (by any of the three calls above): the largest sweep count over the batch
+ * and the total number of 2 x 2 rotations applied (each rotation updates two
+ * rows of H and two columns of H and of V: 60 D + 25 binary64 operations). */
+int mps_hermitian_last_stats(long long* max_sweeps, long long* rotations);
+
+/* |DFT| of each of `count` complex128 records of n_in values zero-padded to
+ * n_out (a power of two, 2 <= n_out <= 2^26, n_out >= n_in):
+ * d_abs[b][f] = |sum_m x_m exp(-2 pi i f m / n_out)|, by a radix-2 FFT.
+ * count <= 65535. */
+int mps_dft_abs_batched(int count, int n_in, const double* d_x, int n_out, double* d_abs, void* stream);
+
 /* Message describing the last error returned on the calling thread. */
 const char* mps_last_error(void);
 

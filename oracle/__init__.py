@@ -58,6 +58,9 @@ def lib():
         L.oracle_svd.argtypes = [I, I, I, dp, dp, dp, dp]
         L.oracle_mps_sample.argtypes = [P, dp, ctypes.c_char_p]
         L.oracle_mps_pauli.argtypes = [P, ctypes.c_char_p, dp]
+        L.oracle_mps_apply_gate_hl.argtypes = [P, I, I, dp, dp]
+        L.oracle_mps_amplitude_hl.argtypes = [P, ctypes.c_char_p, dp]
+        L.oracle_mps_get_schmidt_hl.argtypes = [P, I, dp, dp]
         _lib = L
     return _lib
 
@@ -110,6 +113,32 @@ class OracleMPS:
         rc = lib().oracle_mps_apply_gate(self._h, site, k, _dp(U.view(np.float64)))
         if rc != 0:
             raise RuntimeError("oracle gate failed: %d" % rc)
+
+    def apply_gate_hl(self, site: int, U_hi, U_lo=None) -> None:
+        """Gate whose entries are hi + lo exactly (formed in the oracle's
+        precision; lo may be None)."""
+        hi = _c128(U_hi)
+        k = {2: 1, 4: 2, 8: 3}[hi.shape[0]]
+        lo = None if U_lo is None else _c128(U_lo)
+        rc = lib().oracle_mps_apply_gate_hl(self._h, site, k, _dp(hi.view(np.float64)),
+                                            None if lo is None else _dp(lo.view(np.float64)))
+        if rc != 0:
+            raise RuntimeError("oracle gate failed: %d" % rc)
+
+    def amplitude_hl(self, bits) -> np.ndarray:
+        """<bits|psi> as (re hi, re lo, im hi, im lo): in binary128 mode the
+        value rounded to a pair of doubles."""
+        b = bytes(bytearray(int(x) & 1 for x in bits))
+        out = np.zeros(4)
+        lib().oracle_mps_amplitude_hl(self._h, b, _dp(out))
+        return out
+
+    def schmidt_hl(self, b: int):
+        """(hi, lo) of Lambda_b."""
+        k = self.bond_dim(b)
+        hi, lo = np.zeros(k), np.zeros(k)
+        lib().oracle_mps_get_schmidt_hl(self._h, b, _dp(hi), _dp(lo))
+        return hi, lo
 
     def apply_gate_on(self, qubits, U, route: str = "embed") -> None:
         """Gate on listed qubits (first = most significant). Adjacent increasing

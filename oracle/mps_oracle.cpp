@@ -243,7 +243,10 @@ class OracleBase {
  public:
   virtual ~OracleBase() {}
   virtual int apply(int site, int k, const double* U) = 0;
+  virtual int apply_hl(int site, int k, const double* hi, const double* lo) = 0;
   virtual void amplitude(const unsigned char* bits, double* out) = 0;
+  virtual void amplitude_hl(const unsigned char* bits, double* out) = 0;
+  virtual void schmidt_hl(int b, double* hi, double* lo) const = 0;
   virtual int expectation(int site, int k, const double* O, double* out) = 0;
   virtual int rdo(const int* qubits, int nq, double* rho) = 0;
   virtual void sample(const double* u, unsigned char* bits) = 0;
@@ -283,10 +286,17 @@ class OracleMPS : public OracleBase {
   Cx<R>& g(int s, int i, int a, int c) { return G[s][((size_t)i * cl(s) + a) * cr(s) + c]; }
   Cx<R> gc(int s, int i, int a, int c) const { return G[s][((size_t)i * cl(s) + a) * cr(s) + c]; }
 
-  static Cx<R> in(const double* U, int idx) { return Cx<R>((R)U[2 * idx], (R)U[2 * idx + 1]); }
+  static Cx<R> in(const Cx<R>* U, int idx) { return U[idx]; }
+
+  // a binary128 (or binary64) value as the double pair hi + lo
+  static void split(R x, double* hi, double* lo) {
+    const double h = (double)x;
+    *hi = h;
+    *lo = (double)(x - (R)h);
+  }
 
   // ---- one-site gate: Gamma_s[i] <- sum_k u[i,k] Gamma_s[k]
-  void apply1(int s, const double* U) {
+  void apply1(int s, const Cx<R>* U) {
     const int a_n = cl(s), c_n = cr(s);
     std::vector<Cx<R>> out(G[s].size());
     for (int i = 0; i < 2; ++i)
@@ -301,7 +311,7 @@ class OracleMPS : public OracleBase {
   }
 
   // ---- two-site gate on (s, s+1)
-  int apply2(int s, const double* U) {
+  int apply2(int s, const Cx<R>* U) {
     const int xl = cl(s), xm = cr(s), xr = cr(s + 1);
     const std::vector<R>& ll = lam(s - 1);
     const std::vector<R>& lm = lam(s);
@@ -356,7 +366,7 @@ class OracleMPS : public OracleBase {
   }
 
   // ---- three-site gate on (s, s+1, s+2): one theta, two successive splits
-  int apply3(int s, const double* U) {
+  int apply3(int s, const Cx<R>* U) {
     const int xl = cl(s), x1 = cr(s), x2 = cr(s + 1), xr = cr(s + 2);
     const std::vector<R>& ll = lam(s - 1);
     const std::vector<R>& l1 = lam(s);
@@ -442,14 +452,38 @@ class OracleMPS : public OracleBase {
     return 0;
   }
 
-  int apply(int site, int k, const double* U) override {
-    if (k == 1) { apply1(site, U); return 0; }
-    if (k == 2) return apply2(site, U);
-    return apply3(site, U);
+  int apply(int site, int k, const double* U) override { return apply_hl(site, k, U, nullptr); }
+
+  // gate entries hi + lo (lo may be null), formed exactly in R = binary128
+  int apply_hl(int site, int k, const double* hi, const double* lo) override {
+    const int d = 1 << k;
+    std::vector<Cx<R>> u((size_t)d * d);
+    for (int e = 0; e < d * d; ++e) {
+      R re = (R)hi[2 * e], im = (R)hi[2 * e + 1];
+      if (lo) {
+        re += (R)lo[2 * e];
+        im += (R)lo[2 * e + 1];
+      }
+      u[e] = Cx<R>(re, im);
+    }
+    if (k == 1) { apply1(site, u.data()); return 0; }
+    if (k == 2) return apply2(site, u.data());
+    return apply3(site, u.data());
   }
 
   // <bits|psi> = Gamma_0[b0] Lambda_0 Gamma_1[b1] Lambda_1 ... Gamma_{n-1}[b_{n-1}]
   void amplitude(const unsigned char* bits, double* out) override {
+    const Cx<R> a = amp(bits);
+    out[0] = (double)a.re;
+    out[1] = (double)a.im;
+  }
+  // out = (re hi, re lo, im hi, im lo)
+  void amplitude_hl(const unsigned char* bits, double* out) override {
+    const Cx<R> a = amp(bits);
+    split(a.re, out, out + 1);
+    split(a.im, out + 2, out + 3);
+  }
+  Cx<R> amp(const unsigned char* bits) const {
     std::vector<Cx<R>> v(1, Cx<R>(1));
     for (int s = 0; s < n; ++s) {
       const int a_n = cl(s), c_n = cr(s);
@@ -461,8 +495,7 @@ class OracleMPS : public OracleBase {
       }
       v.swap(w);
     }
-    out[0] = (double)v[0].re;
-    out[1] = (double)v[0].im;
+    return v[0];
   }
 
   // A_t[i] = Gamma_t[i] Lambda_t (right Lambda absorbed); the environment
@@ -673,6 +706,9 @@ class OracleMPS : public OracleBase {
   void schmidt(int b, double* out) const override {
     for (int c = 0; c < chi_[b + 1]; ++c) out[c] = (double)L[b + 1][c];
   }
+  void schmidt_hl(int b, double* hi, double* lo) const override {
+    for (int c = 0; c < chi_[b + 1]; ++c) split(L[b + 1][c], hi + c, lo + c);
+  }
   // chi: n+1 bond dims (boundaries 1), gam: concatenated Gamma_s, lam: concatenated Lambda_0..n-2
   int set_state(const int* chi, const double* gam, const double* lamv) override {
     if (chi[0] != 1 || chi[n] != 1) return -1;
@@ -736,6 +772,17 @@ int oracle_mps_apply_gate(void* h, int site, int k, const double* U) {
   OracleBase* m = static_cast<OracleBase*>(h);
   if (!m || !U || k < 1 || k > 3 || site < 0 || site + k > m->n) return -1;
   return m->apply(site, k, U);
+}
+int oracle_mps_apply_gate_hl(void* h, int site, int k, const double* hi, const double* lo) {
+  OracleBase* o = static_cast<OracleBase*>(h);
+  if (k < 1 || k > 3 || site < 0 || site + k > o->n) return -1;
+  return o->apply_hl(site, k, hi, lo);
+}
+void oracle_mps_amplitude_hl(void* h, const unsigned char* bits, double* out) {
+  static_cast<OracleBase*>(h)->amplitude_hl(bits, out);
+}
+void oracle_mps_get_schmidt_hl(void* h, int b, double* hi, double* lo) {
+  static_cast<OracleBase*>(h)->schmidt_hl(b, hi, lo);
 }
 void oracle_mps_amplitude(void* h, const unsigned char* bits, double* out) {
   static_cast<OracleBase*>(h)->amplitude(bits, out);

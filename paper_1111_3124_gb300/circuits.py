@@ -173,3 +173,127 @@ def random_vidal_state(n: int, chi, rng, decay: float = 8.0):
         x = np.sort(x)[::-1]
         lams.append(x / np.linalg.norm(x))
     return gammas, lams
+
+
+# ---- inputs for the double-word (about 106-bit) path ------------------------
+# A binary64 gate is unitary only to about 1e-16, and a state evolved by such
+# gates is normalised only to that level; to compare results at the 1e-30
+# level the gates themselves must be unitary to that level. dd_unitary
+# re-orthonormalises a binary64 gate's columns by Gram-Schmidt in Python's
+# decimal arithmetic (60 digits) and returns each entry as hi + lo, two
+# doubles whose exact sum is the entry to about 2^-106.
+
+def _dec_split(x):
+    from decimal import Decimal
+    hi = float(x)
+    lo = float(x - Decimal(hi))
+    return hi, lo
+
+
+def dd_unitary(U: np.ndarray):
+    """(U_hi, U_lo), complex128 arrays with U_hi + U_lo unitary to ~1e-32,
+    close to U (a binary64 unitary)."""
+    from decimal import Decimal, localcontext
+    U = np.asarray(U, dtype=np.complex128)
+    d = U.shape[0]
+    with localcontext() as ctx:
+        ctx.prec = 60
+        cols = [[(Decimal(float(U[r, c].real)), Decimal(float(U[r, c].imag))) for r in range(d)] for c in range(d)]
+        out = []
+        for c in range(d):
+            v = cols[c]
+            for q in out:  # v <- v - q (q^H v)
+                pr = sum(a[0] * b[0] + a[1] * b[1] for a, b in zip(q, v))
+                pi = sum(a[0] * b[1] - a[1] * b[0] for a, b in zip(q, v))
+                v = [(b[0] - (a[0] * pr - a[1] * pi), b[1] - (a[0] * pi + a[1] * pr)) for a, b in zip(q, v)]
+            nrm = sum(x * x + y * y for x, y in v).sqrt()
+            out.append([(x / nrm, y / nrm) for x, y in v])
+        hi = np.zeros((d, d), dtype=np.complex128)
+        lo = np.zeros((d, d), dtype=np.complex128)
+        for c in range(d):
+            for r in range(d):
+                rh, rl = _dec_split(out[c][r][0])
+                ih, il = _dec_split(out[c][r][1])
+                hi[r, c] = complex(rh, ih)
+                lo[r, c] = complex(rl, il)
+    return hi, lo
+
+
+def dd_brickwork(n: int, depth: int, rng, rz_after_each: bool = True):
+    """Brickwork of Haar U(4) (with RZ phases after each layer), every gate
+    given as (site, U_hi, U_lo) through dd_unitary."""
+    layers = []
+    for layer in brickwork(n, depth, rng, rz_after_each=rz_after_each):
+        layers.append([(s,) + dd_unitary(U) for s, U in layer])
+    return layers
+
+
+def dd_ghz_prefix(n: int):
+    """H on qubit 0 (entries 1/sqrt(2) as hi + lo), then CNOT(q -> q+1)."""
+    from decimal import Decimal, localcontext
+    with localcontext() as ctx:
+        ctx.prec = 60
+        h, l = _dec_split(Decimal(1) / Decimal(2).sqrt())
+    Hh = np.array([[h, h], [h, -h]], dtype=np.complex128)
+    Hl = np.array([[l, l], [l, -l]], dtype=np.complex128)
+    zero4 = np.zeros((4, 4), dtype=np.complex128)
+    return [[(0, Hh, Hl)]] + [[(q, CNOT.copy(), zero4)] for q in range(n - 1)]
+
+
+# ---- inputs for the Hermitian-matrix workload (the NMR example of Sec. 2.1) --
+# Hamiltonians are in Hz; a state evolves by exp(-2 pi i H t) and the thermal
+# state is exp(-beta H) / Tr with beta = h / (k_B T) (energy h * frequency).
+PLANCK = 6.62606896e-34    # J s, the value Sec. 2.1 prints
+BOLTZMANN = 1.3806504e-23  # J / K, the value Sec. 2.1 prints
+Y90 = np.array([[1, 1], [-1, 1]], dtype=np.complex128) / np.sqrt(2.0)  # the Y_90 pulse of Sec. 2.1
+
+
+def kron_all(*ms):
+    out = np.ones((1, 1), dtype=np.complex128)
+    for m in ms:
+        out = np.kron(out, m)
+    return out
+
+
+def nmr_example():
+    """The two-spin system of Sec. 2.1: a proton (w1 = 400 MHz) and a 13C spin
+    (w2 = 125 MHz) with J12 = 140 kHz at T = 300 K;
+    H = w1 Z(x)I + w2 I(x)Z + J12 Z(x)Z, the Y_90 pulse on the proton, <X> of
+    the proton recorded every dt = 0.145 / w1 for N samples, N the power of
+    two at or above 1 / (dt J12)."""
+    w1, w2, J, T = 400e6, 125e6, 140e3, 300.0
+    H = w1 * np.kron(Z, I2) + w2 * np.kron(I2, Z) + J * np.kron(Z, Z)
+    dt = 0.145 / w1
+    N = 1
+    while N < 1.0 / dt / J:
+        N *= 2
+    return {"H": H, "P": np.kron(Y90, I2), "O": np.kron(X, I2), "beta": PLANCK / BOLTZMANN / T, "dt": dt, "N": N,
+            "w1": w1, "w2": w2, "J": J, "T": T}
+
+
+def spin_hamiltonians(count: int, spins: int, rng, shift_hz: float = 500.0, j_hz: float = 50.0):
+    """`count` strongly coupled spin systems in the rotating frame:
+    H = sum_k o_k Z_k + sum_{k<l} J_kl (X_k X_l + Y_k Y_l + Z_k Z_l) with offsets
+    o_k ~ U[-shift_hz, shift_hz] and couplings J_kl ~ U[-j_hz, j_hz] (Hz);
+    returns (count, 2^spins, 2^spins) complex128."""
+    D = 1 << spins
+    out = np.zeros((count, D, D), dtype=np.complex128)
+
+    def op(P, k):
+        return kron_all(*[P if q == k else I2 for q in range(spins)])
+
+    Zs = [op(Z, k) for k in range(spins)]
+    pairs = [(k, l) for k in range(spins) for l in range(k + 1, spins)]
+    XYZ = {(k, l): op(X, k) @ op(X, l) + op(Y, k) @ op(Y, l) + Zs[k] @ Zs[l] for k, l in pairs}
+    for b in range(count):
+        o = rng.uniform(-shift_hz, shift_hz, spins)
+        H = sum(o[k] * Zs[k] for k in range(spins))
+        for kl in pairs:
+            H = H + rng.uniform(-j_hz, j_hz) * XYZ[kl]
+        out[b] = H
+    return out
+
+
+def random_hermitian(count: int, D: int, rng):
+    g = rng.standard_normal((count, D, D)) + 1j * rng.standard_normal((count, D, D))
+    return np.ascontiguousarray((g + np.conj(np.swapaxes(g, 1, 2))) / 2)

@@ -38,6 +38,11 @@ EXPORTS = [
     "mps_layer_features", "mps_set_predictor", "mps_sketch_stats", "mps_set_limits", "mps_debug_fail_alloc",
     "mps_program_create", "mps_program_run", "mps_program_updates", "mps_program_destroy", "mps_set_tuning",
     "mps_sample", "mps_pauli_expectations", "mps_apply_gate_on",
+    "mps_dd_create", "mps_dd_destroy", "mps_dd_reset", "mps_dd_set_stream", "mps_dd_set_limits",
+    "mps_dd_apply_layer", "mps_dd_apply_layer_device", "mps_dd_sync", "mps_dd_bond_dims", "mps_dd_get_schmidt",
+    "mps_dd_amplitudes", "mps_dd_stats",
+    "mps_heev_batched", "mps_hermitian_function_batched", "mps_fid_batched", "mps_dft_abs_batched",
+    "mps_hermitian_last_stats",
 ]
 
 
@@ -107,6 +112,23 @@ def load_library(path: str = LIB_PATH):
         "mps_program_updates": [P, ctypes.POINTER(ctypes.c_longlong)],
         "mps_program_destroy": [P],
         "mps_debug_fail_alloc": [ctypes.c_longlong],
+        "mps_dd_create": [I, I, D, ctypes.POINTER(P)],
+        "mps_dd_destroy": [P],
+        "mps_dd_reset": [P],
+        "mps_dd_set_stream": [P, P],
+        "mps_dd_set_limits": [P, I],
+        "mps_dd_apply_layer": [P, I, I, ip, dp, dp],
+        "mps_dd_apply_layer_device": [P, I, I, ip, P, P, P],
+        "mps_dd_sync": [P],
+        "mps_dd_bond_dims": [P, ip],
+        "mps_dd_get_schmidt": [P, I, dp, dp, ip],
+        "mps_dd_amplitudes": [P, I, bp, dp],
+        "mps_dd_stats": [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), dp],
+        "mps_heev_batched": [I, I, P, P, P, P],
+        "mps_hermitian_function_batched": [I, I, P, I, D, D, P, P],
+        "mps_fid_batched": [I, I, P, P, P, P, D, I, P, P],
+        "mps_dft_abs_batched": [I, I, P, I, P, P],
+        "mps_hermitian_last_stats": [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -382,6 +404,181 @@ class Program:
         self._h = None
 
     __del__ = close
+
+
+class MPSDD:
+    """An n-qubit MPS in Vidal form held in double-word arithmetic (hi + lo,
+    about 106 bits) on the current CUDA device, chi_max <= 32 (mps_dd_*).
+    Gates are complex128 matrices (U_lo optional low parts)."""
+
+    def __init__(self, n: int, chi_max: int, cutoff: float, stream=None):
+        h = ctypes.c_void_p()
+        check(load_library().mps_dd_create(n, chi_max, float(cutoff), ctypes.byref(h)))
+        self._h = h
+        self.n, self.chi_max, self.cutoff = n, chi_max, cutoff
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load_library().mps_dd_destroy(h)
+        self._h = None
+
+    __del__ = close
+
+    def set_stream(self, stream) -> None:
+        ptr = getattr(stream, "cuda_stream", stream)
+        check(load_library().mps_dd_set_stream(self._h, ctypes.c_void_p(ptr) if ptr else None))
+
+    def set_limits(self, max_sweeps: int) -> None:
+        check(load_library().mps_dd_set_limits(self._h, max_sweeps))
+
+    def reset(self) -> None:
+        check(load_library().mps_dd_reset(self._h))
+
+    def apply_layer(self, sites, Us, Us_lo=None) -> None:
+        Us = _c128(Us)
+        k = {2: 1, 4: 2}[Us.shape[-1]]
+        s = np.ascontiguousarray(np.asarray(sites, dtype=np.int32))
+        lo = None if Us_lo is None else _c128(Us_lo)
+        check(load_library().mps_dd_apply_layer(self._h, k, len(s), _ip(s), _dp(Us.view(np.float64)),
+                                                None if lo is None else _dp(lo.view(np.float64))))
+
+    def apply_layer_device(self, sites, d_sites, d_Us, k: int, d_Us_lo=None) -> None:
+        """d_sites: CUDA int32 tensor; d_Us (and d_Us_lo): CUDA complex128
+        tensors of shape (n_gates, 2^k, 2^k); they must outlive the kernels."""
+        s = np.ascontiguousarray(np.asarray(sites, dtype=np.int32))
+        lo = ctypes.c_void_p(d_Us_lo.data_ptr()) if d_Us_lo is not None else None
+        check(load_library().mps_dd_apply_layer_device(self._h, k, len(s), _ip(s), ctypes.c_void_p(d_sites.data_ptr()),
+                                                       ctypes.c_void_p(d_Us.data_ptr()), lo))
+
+    def run_layers(self, layers) -> int:
+        """Layers of (site, U); within a layer the U(2) gates are applied
+        before the U(4) gates (they act on disjoint qubits). Returns the
+        number of two-site updates."""
+        nup = 0
+        for layer in layers:
+            by_k = {}
+            for site, U in layer:
+                by_k.setdefault(U.shape[0], []).append((site, U))
+            for d in sorted(by_k):
+                gs = by_k[d]
+                self.apply_layer([s for s, _ in gs], np.stack([_c128(U) for _, U in gs]))
+                if d == 4:
+                    nup += len(gs)
+        return nup
+
+    def sync(self) -> None:
+        check(load_library().mps_dd_sync(self._h))
+
+    def bond_dims(self) -> np.ndarray:
+        chi = np.zeros(self.n + 1, dtype=np.int32)
+        check(load_library().mps_dd_bond_dims(self._h, _ip(chi)))
+        return chi
+
+    def schmidt(self, bond: int):
+        """(hi, lo) arrays of Lambda_bond."""
+        hi = np.zeros(self.chi_max)
+        lo = np.zeros(self.chi_max)
+        k = ctypes.c_int()
+        check(load_library().mps_dd_get_schmidt(self._h, bond, _dp(hi), _dp(lo), ctypes.byref(k)))
+        return hi[:k.value].copy(), lo[:k.value].copy()
+
+    def amplitudes(self, bits) -> np.ndarray:
+        """(count, 4) array: re hi, re lo, im hi, im lo."""
+        b = np.ascontiguousarray(np.asarray(bits, dtype=np.uint8).reshape(-1, self.n))
+        out = np.zeros((b.shape[0], 4))
+        check(load_library().mps_dd_amplitudes(self._h, b.shape[0], b.ctypes.data_as(ctypes.c_char_p), _dp(out)))
+        return out
+
+    def stats(self) -> dict:
+        u, s = ctypes.c_longlong(), ctypes.c_longlong()
+        f = ctypes.c_double()
+        check(load_library().mps_dd_stats(self._h, ctypes.byref(u), ctypes.byref(s), ctypes.byref(f)))
+        return {"updates": u.value, "sweeps": s.value, "flops": f.value}
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_ptr(stream):
+    ptr = getattr(stream, "cuda_stream", stream)
+    return ctypes.c_void_p(ptr) if ptr else None
+
+
+def _herm_batch(H):
+    import torch
+    H = H.to(torch.complex128).contiguous()
+    if H.dim() == 2:
+        H = H.unsqueeze(0)
+    assert H.is_cuda and H.shape[-1] == H.shape[-2]
+    return H
+
+
+def heev(H, stream=None):
+    """Eigenvalues (ascending) and eigenvectors (columns) of Hermitian CUDA
+    matrices H (..., D, D) by the batched two-sided Jacobi kernel."""
+    import torch
+    Hb = _herm_batch(H)
+    b, D = Hb.shape[0], Hb.shape[-1]
+    w = torch.empty((b, D), dtype=torch.float64, device=Hb.device)
+    V = torch.empty((b, D, D), dtype=torch.complex128, device=Hb.device)
+    check(load_library().mps_heev_batched(b, D, _dptr(Hb), _dptr(w), _dptr(V), _stream_ptr(stream)))
+    return w, V
+
+
+def expm_hermitian(H, a: complex, stream=None):
+    """exp(a H) for Hermitian CUDA matrices H (..., D, D), complex scalar a."""
+    import torch
+    Hb = _herm_batch(H)
+    out = torch.empty_like(Hb)
+    a = complex(a)
+    check(load_library().mps_hermitian_function_batched(Hb.shape[0], Hb.shape[-1], _dptr(Hb), 0, a.real, a.imag,
+                                                        _dptr(out), _stream_ptr(stream)))
+    return out
+
+
+def thermal_state(H, beta: float, stream=None):
+    """exp(-beta H) / Tr exp(-beta H) for Hermitian CUDA matrices H."""
+    import torch
+    Hb = _herm_batch(H)
+    out = torch.empty_like(Hb)
+    check(load_library().mps_hermitian_function_batched(Hb.shape[0], Hb.shape[-1], _dptr(Hb), 1, float(beta), 0.0,
+                                                        _dptr(out), _stream_ptr(stream)))
+    return out
+
+
+def fid(rho, H, O, dt: float, N: int, P=None, stream=None):
+    """Tr(exp(-iHt) P rho P^H exp(iHt) O) at t = m dt, m < N: (batch, N) complex128."""
+    import torch
+    r, Hb, Ob = _herm_batch(rho), _herm_batch(H), _herm_batch(O)
+    Pb = _herm_batch(P) if P is not None else None
+    b, D = Hb.shape[0], Hb.shape[-1]
+    sig = torch.empty((b, N), dtype=torch.complex128, device=Hb.device)
+    check(load_library().mps_fid_batched(b, D, _dptr(r), _dptr(Hb), _dptr(Ob), _dptr(Pb), float(dt), int(N),
+                                         _dptr(sig), _stream_ptr(stream)))
+    return sig
+
+
+def hermitian_last_stats() -> dict:
+    """Largest sweep count and total rotations of the last diagonalisation."""
+    sw, rot = ctypes.c_longlong(), ctypes.c_longlong()
+    check(load_library().mps_hermitian_last_stats(ctypes.byref(sw), ctypes.byref(rot)))
+    return {"max_sweeps": sw.value, "rotations": rot.value}
+
+
+def dft_abs(x, n_out: int, stream=None):
+    """|DFT| of complex CUDA records x (batch, n_in) zero-padded to n_out."""
+    import torch
+    xb = x.to(torch.complex128).contiguous()
+    if xb.dim() == 1:
+        xb = xb.unsqueeze(0)
+    out = torch.empty((xb.shape[0], n_out), dtype=torch.float64, device=xb.device)
+    check(load_library().mps_dft_abs_batched(xb.shape[0], xb.shape[1], _dptr(xb), int(n_out), _dptr(out),
+                                             _stream_ptr(stream)))
+    return out
 
 
 def circuit_passes(layers, owner: int = 0, device="cuda"):
