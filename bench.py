@@ -109,6 +109,10 @@ def args_parse():
     p.add_argument("--retune", action="store_true", help="ignore the tuner's cache")
     p.add_argument("--chi", type=int, default=256, help="bond dimension of the saturated-layer case")
     p.add_argument("--layers", type=int, default=1, help="layers of the saturated-layer case")
+    p.add_argument("--profile-dd", action="store_true",
+                   help="run the double-word capture case (2 circuits, n=32, chi_max=32, 8 layers)")
+    p.add_argument("--profile-hermitian", action="store_true",
+                   help="run the Hermitian-workload capture case (1024 five-spin systems)")
     return p.parse_args()
 
 
@@ -246,22 +250,22 @@ def run_reference(a):
 
 # ----------------------------------------------------------- nominal work ---
 
-def nominal_update_flops(chi_l: int, chi_m: int, chi_r: int) -> float:
+def nominal_update_flops(chi_l: int, chi_m: int, chi_r: int):
     """Nominal binary64 work of one two-site update on bonds (chi_l, chi_m,
-    chi_r): theta as a complex GEMM, 8 flops per multiply-add over
-    (2 chi_l) x (2 chi_r) x chi_m, plus the SVD of the complex M x N theta by
-    the Golub-Reinsch count 4 (14 M N^2 + 8 N^3), M >= N. At chi = 256
-    everywhere: 32 chi^3 + 704 chi^3 = 12.4 GFLOP."""
+    chi_r): (theta, svd) with theta as a complex GEMM, 8 flops per
+    multiply-add over (2 chi_l) x (2 chi_r) x chi_m, and the SVD of the
+    complex M x N theta by the Golub-Reinsch count 4 (14 M N^2 + 8 N^3),
+    M >= N. At chi = 256 everywhere: 32 chi^3 + 704 chi^3 = 12.4 GFLOP."""
     m, n = 2 * chi_l, 2 * chi_r
     if m < n:
         m, n = n, m
-    return 8.0 * m * n * chi_m + 4.0 * (14.0 * m * n * n + 8.0 * n ** 3)
+    return 8.0 * m * n * chi_m, 4.0 * (14.0 * m * n * n + 8.0 * n ** 3)
 
 
-def step_nominal_flops(m, dev_layers, n: int) -> float:
+def step_nominal_flops(m, dev_layers, n: int) -> dict:
     """One untimed pass of the circuit, summing the nominal work of every
     two-site update from the bond dimensions before its layer."""
-    total = 0.0
+    theta = svd = 0.0
     m.reset()
     for k, s, dU in dev_layers:
         if k == 2:
@@ -269,10 +273,12 @@ def step_nominal_flops(m, dev_layers, n: int) -> float:
             for site in s.tolist():
                 chi_l = int(bd[site - 1]) if site > 0 else 1
                 chi_r = int(bd[site + 1]) if site + 1 < n - 1 else 1
-                total += nominal_update_flops(chi_l, int(bd[site]), chi_r)
+                t, v = nominal_update_flops(chi_l, int(bd[site]), chi_r)
+                theta += t
+                svd += v
         m.apply_layer_device(s, dU, k)
     m.sync()
-    return total
+    return {"total": theta + svd, "theta": theta, "svd": svd}
 
 
 # ------------------------------------------------------------ multi-rank ---
@@ -445,6 +451,156 @@ def run_routing(prec, tune_table=()):
     return out
 
 
+def run_dd(fp64_peak_tflops: float, circuits: int = 8, steps: int = 2, depth: int = 20):
+    """Beyond binary64: `circuits` independent n = 32, depth-20 circuits of
+    Haar U(4) gates with RZ phases (gates unitary to ~1e-32, given as hi + lo),
+    chi_max = 32, cutoff 1e-28, each on its own double-word handle and CUDA
+    stream, gates resident on the device; plus the error against the oracle
+    in binary128 on an n = 8 circuit of the same kind."""
+    import torch
+    import oracle
+    from paper_1111_3124_gb300 import circuits as C
+    from paper_1111_3124_gb300.mps import MPSDD
+    n, chi, cutoff = 32, 32, 1e-28
+    circs = [C.dd_brickwork(n, depth, np.random.default_rng(C.SEED_BASE + 7000 + i)) for i in range(circuits)]
+    dev = []  # per circuit: list of (k, sites, d_sites, d_hi, d_lo)
+    for layers in circs:
+        steps_c = []
+        for layer in layers:
+            by_d = {}
+            for site, Uh, Ul in layer:
+                by_d.setdefault(Uh.shape[0], []).append((site, Uh, Ul))
+            for d in sorted(by_d):
+                g = by_d[d]
+                sites = [s for s, _, _ in g]
+                steps_c.append(({2: 1, 4: 2}[d], sites, torch.tensor(sites, dtype=torch.int32, device="cuda"),
+                                torch.from_numpy(np.stack([u for _, u, _ in g])).cuda(),
+                                torch.from_numpy(np.stack([l for _, _, l in g])).cuda()))
+        dev.append(steps_c)
+    streams = [torch.cuda.Stream() for _ in range(circuits)]
+    hs = [MPSDD(n, chi, cutoff, stream=streams[i]) for i in range(circuits)]
+
+    def one_step():
+        for h in hs:
+            h.reset()
+        for li in range(len(dev[0])):
+            for h, steps_c in zip(hs, dev):
+                k, sites, d_s, d_hi, d_lo = steps_c[li]
+                h.apply_layer_device(sites, d_s, d_hi, k, d_lo)
+        for h in hs:
+            h.sync()
+
+    one_step()  # warm-up
+    ts, flops, upd = [], 0.0, 0
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        one_step()
+        ts.append(time.perf_counter() - t0)
+        for h in hs:
+            st = h.stats()
+            flops += st["flops"]
+            upd += st["updates"]
+    t = sum(ts)
+    tflops = flops / t / 1e12
+    chi_end = hs[0].bond_dims()
+    for h in hs:
+        h.close()
+    # accuracy against the oracle in binary128 (n = 8, depth 8, chi_max = 16)
+    nsm = 8
+    small = C.dd_brickwork(nsm, 8, np.random.default_rng(C.SEED_BASE + 7999))
+    m = MPSDD(nsm, 16, cutoff)
+    o = oracle.OracleMPS(nsm, 16, cutoff, oracle.BINARY128)
+    for layer in small:
+        by_d = {}
+        for site, Uh, Ul in layer:
+            by_d.setdefault(Uh.shape[0], []).append((site, Uh, Ul))
+            o.apply_gate_hl(site, Uh, Ul)
+        for d in sorted(by_d):
+            g = by_d[d]
+            m.apply_layer([s for s, _, _ in g], np.stack([u for _, u, _ in g]), np.stack([l for _, _, l in g]))
+    err = 0.0
+    for b in range(nsm - 1):
+        hi, lo = m.schmidt(b)
+        ohi, olo = o.schmidt_hl(b)
+        if len(hi) != len(ohi):
+            err = float("inf")
+            break
+        err = max(err, float(np.max(np.abs((hi - ohi) + (lo - olo))) / ohi[0]))
+    m.close()
+    return {"workload": "%d circuits: n=32, depth-%d Haar U(4) brickwork + RZ, chi_max=32, cutoff 1e-28, "
+                        "gates unitary to 1e-32 (hi + lo)" % (circuits, depth),
+            "value": upd / t, "unit": "updates/s", "steps": steps, "warmup": 1, "updates_per_step": upd // steps,
+            "max_bond": int(chi_end.max()), "timing": "wall clock around the layers of all circuits + sync",
+            "executed_binary64_tflops": tflops, "peak_fp64_tflops": fp64_peak_tflops,
+            "frac_of_measured_fp64": tflops / fp64_peak_tflops,
+            "oracle_binary128_spectrum_err": err,
+            "oracle_case": "n=8, depth-8 brickwork + RZ, chi_max=16: max |d lambda| / lambda_0 over all bonds"}
+
+
+def run_hermitian(fp64_peak_tflops: float, count: int = 4096, spins: int = 5, N: int = 2048):
+    """The matrix library's second workload (Sec. 2.1's NMR example, batched):
+    `count` strongly coupled `spins`-spin systems (D = 2^spins): thermal state
+    (its deviation from I/D) at 300 K, Y_90 pulse on every spin, record of the total X magnetisation
+    (N samples, dt = 0.25 ms), zero padding to 2N and |DFT|, every step on the
+    GPU; the Jacobi eigensolver's executed flops from its rotation count."""
+    import torch
+    from oracle import hermitian as O
+    from paper_1111_3124_gb300 import circuits as C
+    from paper_1111_3124_gb300.mps import dft_abs, fid, heev, hermitian_last_stats, thermal_deviation
+    D = 1 << spins
+    H = C.spin_hamiltonians(count, spins, np.random.default_rng(C.SEED_BASE + 8000))
+    P = C.kron_all(*[C.Y90] * spins)
+    Ox = sum(C.kron_all(*[C.X if q == k else C.I2 for q in range(spins)]) for k in range(spins))
+    Hd = torch.from_numpy(H).cuda()
+    H2 = (2 * np.pi) * Hd
+    Pd = torch.from_numpy(np.broadcast_to(P, H.shape).copy()).cuda()
+    Od = torch.from_numpy(np.broadcast_to(Ox, H.shape).copy()).cuda()
+    beta = C.PLANCK / C.BOLTZMANN / 300.0
+    dt = 2.5e-4
+
+    def pipeline():
+        # rho - I/D: the record of the traceless X_total depends on it alone,
+        # and at 300 K it sits in the 10th digit of rho's entries
+        rho = thermal_deviation(Hd, beta)
+        s = fid(rho, H2, Od, dt, N, P=Pd)
+        return rho, s, dft_abs(s, 2 * N)
+
+    pipeline()  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rho, s, spec = pipeline()
+    torch.cuda.synchronize()
+    t_all = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    heev(Hd)
+    torch.cuda.synchronize()
+    t_heev = time.perf_counter() - t0
+    st = hermitian_last_stats()
+    flops = st["rotations"] * (60.0 * D + 25.0)
+    # accuracy against the oracle on the first 4 systems
+    rho_h, s_h, sp_h = rho[:4].cpu().numpy(), s[:4].cpu().numpy(), spec[:4].cpu().numpy()
+    ms = [0, 1, N // 2, N - 1]
+    err_rho = err_fid = err_dft = 0.0
+    for b in range(4):
+        r_ref = O.thermal_deviation(H[b], beta)
+        err_rho = max(err_rho, float(np.max(np.abs(rho_h[b] - r_ref)) / np.max(np.abs(r_ref))))
+        f_ref = O.fid(r_ref, 2 * np.pi * H[b], Ox, dt, ms, P=P)
+        err_fid = max(err_fid, float(np.max(np.abs(s_h[b, ms] - f_ref)) / np.max(np.abs(f_ref))))
+        d_ref = O.dft_abs(s_h[b], 2 * N)
+        err_dft = max(err_dft, float(np.max(np.abs(sp_h[b] - d_ref)) / np.max(d_ref)))
+    return {"workload": "%d strongly coupled %d-spin systems (D=%d), 300 K, Y90 pulses, <X_total> record N=%d, "
+                        "zero-padded |DFT| of 2N" % (count, spins, D, N),
+            "value": count / t_all, "unit": "systems/s", "seconds_pipeline": t_all, "seconds_heev": t_heev,
+            "heev": {"kernel": "k_heev (batched two-sided Jacobi, binary64)", "max_sweeps": st["max_sweeps"],
+                     "rotations": st["rotations"], "executed_tflops": flops / t_heev / 1e12,
+                     "peak_fp64_tflops": fp64_peak_tflops, "frac": flops / t_heev / 1e12 / fp64_peak_tflops,
+                     "flops_per_rotation": "60 D + 25"},
+            "oracle_err": {"thermal_deviation_rel": err_rho, "fid_rel": err_fid, "dft_rel": err_dft, "systems": 4},
+            "timing": "wall clock around the calls (each synchronises)"}
+
+
 def run_gpu(a):
     import torch
     import torch.distributed as dist
@@ -612,8 +768,18 @@ def run_gpu(a):
     }
     dom = max(roof_def, key=lambda i: prof[i]["ms"])
     d = prof[dom]
-    achieved = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else None
+    executed = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else None
     name, bound, peak, src = roof_def[dom]
+    # algorithmic work: the nominal SVD count of every update of the step
+    # charged to the dominant Jacobi kernel's time (its launches carry the
+    # SVD); for the tensor-core GEMM its slice products are the algorithm
+    if dom in (0, 4) and nominal is not None and d["ms"] > 0:
+        achieved = nominal["svd"] / (d["ms"] / 1e3) / 1e12
+        algorithmic = ("Golub-Reinsch count 4 (14 M N^2 + 8 N^3) of every update's M x N SVD in one step "
+                       "(%.1f GFLOP), over this kernel class's time per step" % (nominal["svd"] / 1e9))
+    else:
+        achieved = executed
+        algorithmic = "tensor-core flops of the slice products"
     # DRAM bytes per launch from one ncu capture of a saturated chi=256 layer
     # (the --profile-layer case), scaled to this run's average launch by
     # duration (both Jacobi kernels are ALU-bound: time tracks work)
@@ -621,10 +787,13 @@ def run_gpu(a):
     ms_launch = d["ms"] / max(d["launches"], 1)
     traffic = captured[dom][0] * ms_launch / captured[dom][1] if dom in captured else None
     roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if achieved else None, "peak_source": src,
-            "flops_per_launch": d["flops"] / max(d["launches"], 1),
-            "flops_counted": "executed flops counted on the device (Gram, inner rotations, column rotations)"
-            if dom in (0, 4) else "tensor-core flops of the slice products",
+            "frac": achieved / peak if achieved else None, "peak_source": src, "achieved_is": algorithmic,
+            "algorithmic_flops_per_launch": achieved * 1e12 * (d["ms"] / 1e3) / max(d["launches"], 1)
+            if achieved else None,
+            "executed": {"tflops": executed, "frac": executed / peak if executed else None,
+                         "flops_per_launch": d["flops"] / max(d["launches"], 1),
+                         "counted": "flops executed, counted on the device (Gram, inner rotations, column "
+                                    "rotations)" if dom in (0, 4) else "tensor-core flops of the slice products"},
             "ms_per_launch": ms_launch, "traffic": traffic,
             "traffic_source": "ncu dram__bytes_read+write of a saturated launch, scaled by duration"
             if traffic is not None else None,
@@ -658,13 +827,15 @@ def run_gpu(a):
     if nominal:
         # nominal binary64 work (theta GEMM + Golub-Reinsch SVD count) per second:
         # what a binary64 Golub-Reinsch SVD path would have to sustain to match
+        nt = nominal["total"]
         line["nominal_binary64"] = {
-            "gflop_per_step": nominal / 1e9, "tflops": nominal / t_step / 1e12,
-            "peak_fp64_tflops": pk["fp64_tflops"], "frac_of_fp64_peak": nominal / t_step / 1e12 / pk["fp64_tflops"],
+            "gflop_per_step": nt / 1e9, "svd_gflop_per_step": nominal["svd"] / 1e9, "tflops": nt / t_step / 1e12,
+            "peak_fp64_tflops": alu["fp64_tflops"], "frac_of_fp64_peak": nt / t_step / 1e12 / alu["fp64_tflops"],
+            "peak_source": "measured binary64 GEMM throughput",
             "definition": "reference-algorithm-equivalent rate, not executed flops: per update 8*M*N*chi + "
                           "4*(14*M*N^2 + 8*N^3), theta M x N = 2chi_L x 2chi_R"}
         if fp64 is not None:
-            fp64["nominal_binary64_tflops"] = nominal / (fp64["ms_per_step"] / 1e3) / 1e12
+            fp64["nominal_binary64_tflops"] = nt / (fp64["ms_per_step"] / 1e3) / 1e12
     if rank == 0 and world == 1:
         if not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_obj(a.cpu_sample)
@@ -674,6 +845,8 @@ def run_gpu(a):
             line["three_site"] = run_config3(prec, 2, tune_table)
             line["many_circuits"] = run_config4(prec, a.batch_circuits, 1, tune_table)
             line["routing"] = run_routing(prec, tune_table)
+            line["double_word"] = run_dd(alu["fp64_tflops"])
+            line["hermitian"] = run_hermitian(alu["fp64_tflops"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if prog is not None:
@@ -710,12 +883,31 @@ def run_profile_layer(a):
     m.close()
 
 
+def run_profile_small(a):
+    """The capture cases of the double-word path and the Hermitian workload:
+    small versions of the `double_word` and `hermitian` lines."""
+    import torch
+    from paper_1111_3124_gb300 import build as B
+    torch.cuda.set_device(0)
+    B.build()
+    t0 = time.perf_counter()
+    if a.profile_dd:
+        out = run_dd(1.0, circuits=2, steps=1, depth=8)
+    else:
+        out = run_hermitian(1.0, count=1024, N=512)
+    print("%s: %.3f s, %s %s" % ("double-word" if a.profile_dd else "hermitian", time.perf_counter() - t0,
+                                 out["value"], out["unit"]))
+
+
 def main():
     global ARGS
     a = args_parse()
     ARGS = a
     if a.profile_layer:
         run_profile_layer(a)
+        return
+    if a.profile_dd or a.profile_hermitian:
+        run_profile_small(a)
         return
     if a.impl == "reference":
         import oracle

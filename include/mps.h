@@ -515,7 +515,13 @@ int mps_heev_batched(int count, int D, const double* d_H, double* d_w, double* d
  * Sec. 2.1; a = -i t gives the propagator exp(-i H t)).
  * kind 1: d_out = exp(-beta H) / Tr exp(-beta H) with beta = a_re (the
  * thermal state), computed in H's eigenbasis with the weights shifted so that
- * the largest is 1. */
+ * the largest is 1.
+ * kind 2: d_out = exp(-beta H) / Tr exp(-beta H) - I / D (beta = a_re), the
+ * deviation from the infinite-temperature state, with the weights formed by
+ * expm1 so that it keeps full relative accuracy when beta ||H|| is small (at
+ * 300 K and Hz-scale H the thermal state's entries differ from 1/D only in
+ * the 10th or later digit, and the record of a traceless observable depends
+ * on that difference alone). */
 int mps_hermitian_function_batched(int count, int D, const double* d_H, int kind, double a_re, double a_im,
                                    double* d_out, void* stream);
 

@@ -32,6 +32,17 @@ def thermal(H, beta: float):
     return E / np.trace(E).real
 
 
+def thermal_deviation(H, beta: float):
+    """exp(-beta H) / Tr - I/D in H's eigenbasis, the weights written as
+    (e_k - mean e) / (D (1 + mean e)) with e_k = expm1(-beta (lambda_k - lambda_0)),
+    which is p_k - 1/D exactly and free of cancellation against 1/D."""
+    w, V = heev(H)
+    D = len(w)
+    e = np.expm1(-beta * (w - w[0]))
+    dev = (e - e.mean()) / (D * (1.0 + e.mean()))
+    return (V * dev[None, :]) @ V.conj().T
+
+
 def fid(rho, H, O, dt: float, ms, P=None):
     """Tr(exp(-i H t) rho' exp(i H t) O) at t = m dt for m in ms, rho' = P rho P^H."""
     rho = np.asarray(rho, dtype=np.complex128)

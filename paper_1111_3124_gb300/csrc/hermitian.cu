@@ -193,8 +193,9 @@ __global__ void __launch_bounds__(kHThreads) k_heev(int D, const double2* __rest
   }
 }
 
-// out = V diag(f) V^H with f_k = exp(a lambda_k) (kind 0, a complex) or the
-// Boltzmann weights exp(-beta (lambda_k - lambda_0)) / Z (kind 1, beta = a.x).
+// out = V diag(f) V^H with f_k = exp(a lambda_k) (kind 0, a complex), the
+// Boltzmann weights exp(-beta (lambda_k - lambda_0)) / Z (kind 1, beta = a.x),
+// or those weights minus 1/D (kind 2, the thermal state minus I/D).
 __global__ void k_hfun(int D, const double* __restrict__ w, const double2* __restrict__ V, int kind, double2 a,
                        double2* __restrict__ out) {
   __shared__ double2 fk[kHMaxD];
@@ -210,13 +211,21 @@ __global__ void k_hfun(int D, const double* __restrict__ w, const double2* __res
       fk[tid] = make_double2(mag * cs, mag * sn);
     } else {
       const double ref = a.x >= 0.0 ? wb[0] : wb[D - 1];  // the largest weight is 1
-      fk[tid] = make_double2(exp(-a.x * (wb[tid] - ref)), 0.0);
+      // kind 1: e^{-beta (lambda_k - ref)}; kind 2: expm1 of the same exponent
+      fk[tid] = make_double2(kind == 1 ? exp(-a.x * (wb[tid] - ref)) : expm1(-a.x * (wb[tid] - ref)), 0.0);
     }
   }
   __syncthreads();
   if (tid == 0) {
     double z = 0.0;
     for (int k = 0; k < D; ++k) z += fk[k].x;
+    if (kind == 2) {
+      // p_k - 1/D = (e_k - mean e) / (D (1 + mean e)) with e_k = expm1(...):
+      // no cancellation against 1/D when beta (lambda - ref) is small
+      const double mean = z / D;
+      for (int k = 0; k < D; ++k) fk[k].x -= mean;
+      z = D * (1.0 + mean);
+    }
     Z = kind == 0 ? 1.0 : z;
   }
   __syncthreads();
@@ -463,7 +472,7 @@ int mps_hermitian_function_batched(int count, int D, const double* d_H, int kind
                                    double* d_out, void* stream) {
   int rc = check_dims(count, D);
   if (rc != MPS_OK) return rc;
-  if (!d_H || !d_out || (kind != 0 && kind != 1)) return h_fail(MPS_ERR_ARG, "bad argument");
+  if (!d_H || !d_out || kind < 0 || kind > 2) return h_fail(MPS_ERR_ARG, "bad argument");
   cudaStream_t st = (cudaStream_t)stream;
   Scratch sc;
   double* w = nullptr;

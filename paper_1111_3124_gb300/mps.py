@@ -550,6 +550,16 @@ def thermal_state(H, beta: float, stream=None):
     return out
 
 
+def thermal_deviation(H, beta: float, stream=None):
+    """exp(-beta H) / Tr exp(-beta H) - I/D, accurate when beta ||H|| is small."""
+    import torch
+    Hb = _herm_batch(H)
+    out = torch.empty_like(Hb)
+    check(load_library().mps_hermitian_function_batched(Hb.shape[0], Hb.shape[-1], _dptr(Hb), 2, float(beta), 0.0,
+                                                        _dptr(out), _stream_ptr(stream)))
+    return out
+
+
 def fid(rho, H, O, dt: float, N: int, P=None, stream=None):
     """Tr(exp(-iHt) P rho P^H exp(iHt) O) at t = m dt, m < N: (batch, N) complex128."""
     import torch

@@ -77,10 +77,10 @@ def test_nominal_work_count():
     sys.path.insert(0, ROOT)
     import numpy as np
     import bench
-    assert bench.nominal_update_flops(256, 256, 256) == 736 * 256 ** 3
+    assert bench.nominal_update_flops(256, 256, 256) == (32 * 256 ** 3, 704 * 256 ** 3)
     assert bench.nominal_update_flops(4, 8, 16) == bench.nominal_update_flops(16, 8, 4)
     m_, n_ = 32, 8  # chi_l = 16, chi_r = 4
-    assert bench.nominal_update_flops(16, 8, 4) == 8 * m_ * n_ * 8 + 4 * (14 * m_ * n_ ** 2 + 8 * n_ ** 3)
+    assert bench.nominal_update_flops(16, 8, 4) == (8 * m_ * n_ * 8, 4 * (14 * m_ * n_ ** 2 + 8 * n_ ** 3))
 
     class Stub:  # bond dimensions 2, 3, 5 of a 4-site chain; records the calls
         def __init__(self):
@@ -102,7 +102,8 @@ def test_nominal_work_count():
               (2, np.array([1], dtype=np.int32), None)]
     stub = Stub()
     got = bench.step_nominal_flops(stub, layers, 4)
-    want = (bench.nominal_update_flops(1, 2, 3) + bench.nominal_update_flops(3, 5, 1)
-            + bench.nominal_update_flops(2, 3, 5))
-    assert got == want
+    parts = [bench.nominal_update_flops(1, 2, 3), bench.nominal_update_flops(3, 5, 1),
+             bench.nominal_update_flops(2, 3, 5)]
+    assert got["theta"] == sum(t for t, _ in parts) and got["svd"] == sum(v for _, v in parts)
+    assert got["total"] == got["theta"] + got["svd"]
     assert stub.calls == ["reset", (2, (0, 2)), (1, (0, 1, 2, 3)), (2, (1,)), "sync"]

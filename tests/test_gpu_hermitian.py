@@ -135,3 +135,27 @@ def test_argument_checks():
     with pytest.raises(MPSError) as e:
         dft_abs(torch.zeros((1, 10), dtype=torch.complex128, device="cuda"), 12)
     assert e.value.code == MPS_ERR_ARG
+
+
+def test_thermal_deviation_at_300K_and_its_record():
+    """At 300 K with Hz-scale couplings the thermal state differs from I/D in
+    the 10th digit; its deviation (kind 2, expm1 weights) keeps full relative
+    accuracy, and so does the record of a traceless observable built on it."""
+    from paper_1111_3124_gb300.mps import fid, thermal_deviation
+    spins = 4
+    H = C.spin_hamiltonians(16, spins, np.random.default_rng(12))
+    beta = C.PLANCK / C.BOLTZMANN / 300.0
+    dev = thermal_deviation(_dev(H), beta)
+    dev_h = dev.cpu().numpy()
+    P = C.kron_all(*[C.Y90] * spins)
+    Ox = sum(C.kron_all(*[C.X if q == k else C.I2 for q in range(spins)]) for k in range(spins))
+    dt, N = 2.5e-4, 512
+    s = fid(dev, _dev(2 * np.pi * H), _dev(np.broadcast_to(Ox, H.shape).copy()), dt, N,
+            P=_dev(np.broadcast_to(P, H.shape).copy())).cpu().numpy()
+    ms = [0, 7, 511]
+    for b in range(H.shape[0]):
+        ref = O.thermal_deviation(H[b], beta)
+        scale = np.max(np.abs(ref))
+        assert np.max(np.abs(dev_h[b] - ref)) < 1e-12 * scale
+        fr = O.fid(ref, 2 * np.pi * H[b], Ox, dt, ms, P=P)
+        assert np.max(np.abs(s[b, ms] - fr)) < 1e-11 * np.max(np.abs(fr))

@@ -5,6 +5,7 @@ exponential of a Pauli matrix, the Boltzmann weights of a diagonal H, the
 analytic free-induction decay of the paper's two-spin example, and a pure
 tone's DFT with Parseval's identity."""
 import numpy as np
+import pytest
 
 from oracle import hermitian as O
 from paper_1111_3124_gb300 import circuits as C
@@ -70,3 +71,25 @@ def test_dft_of_a_pure_tone_and_parseval():
     assert abs(X[f0] - n_in) < 1e-9
     assert np.argmax(X) == f0
     assert abs(np.sum(X ** 2) - n_out * np.sum(np.abs(x) ** 2)) < 1e-8 * n_out * n_in
+
+
+def test_thermal_deviation_against_mpmath_at_300K():
+    """rho - I/D at 300 K for Hz-scale couplings (beta ||H|| ~ 1e-10): the
+    oracle's expm1 form against exp(-beta H) / Tr - I/D evaluated by mpmath at
+    60 digits (where the cancellation against 1/D costs nothing)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 60
+    H = C.spin_hamiltonians(1, 3, np.random.default_rng(8))[0]
+    beta = C.PLANCK / C.BOLTZMANN / 300.0
+    dev = O.thermal_deviation(H, beta)
+    M = mpmath.matrix([[mpmath.mpc(H[r, c].real, H[r, c].imag) for c in range(8)] for r in range(8)])
+    E = mpmath.expm(-mpmath.mpf(beta) * M)
+    tr = sum(E[i, i] for i in range(8))
+    ref = np.array([[complex((E[r, c] / tr - (1 if r == c else 0) / mpmath.mpf(8))) for c in range(8)]
+                    for r in range(8)])
+    scale = np.max(np.abs(ref))
+    assert scale < 1e-9  # the deviation is tiny against 1/D
+    assert np.max(np.abs(dev - ref)) < 1e-13 * scale
+    # the plain formula loses most digits of it
+    plain = O.thermal(H, beta) - np.eye(8) / 8
+    assert np.max(np.abs(plain - ref)) > 1e-9 * scale
