@@ -12,6 +12,9 @@
 // Kernels (one CTA per gate of a layer of disjoint gates):
 //   k_dd_theta  - theta of (s, s+1) with the Lambda weights and the gate, into
 //                 the Jacobi working matrix (theta, or theta^H when wide)
+//   k_dd_precondition - binary64 sweeps on the high parts, then A <- A V1
+//                 with V1 the binary64 right factor made unitary in
+//                 double-word (the double-word sweeps start nearly converged)
 //   k_dd_jacobi - cyclic one-sided Jacobi in round-robin order: each warp
 //                 takes one column pair of a round, lanes stride the rows,
 //                 the three inner products are reduced across the warp by
@@ -161,6 +164,179 @@ __device__ __forceinline__ void warp_sum_dd(dd& v) {
   for (int m = 16; m >= 1; m >>= 1) v = dd_add(v, shfl_xor_dd(v, m));
 }
 
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
+constexpr double kEps64 = 1.1102230246251565e-16;  // 2^-53
+constexpr int kDdPreSweeps = 40;                   // binary64 sweep limit of the preconditioner
+constexpr size_t kDdPreSmem = 2 * (size_t)kDdW * kDdW * sizeof(double2);
+
+// Preconditioner of the double-word Jacobi (one CTA per gate). The binary64
+// sweeps do most of the orthogonalisation at a fraction of the double-word
+// cost; the double-word sweeps that follow only have to remove what binary64
+// cannot resolve (off-diagonals ~1e-15 -> ~1e-30: quadratic convergence).
+//   1. Binary64 cyclic one-sided Jacobi on the high parts of A (shared
+//      memory), accumulating V64 (unitary to ~1e-15).
+//   2. V64 made unitary to double-word accuracy: with E = V64^H V64 - I
+//      (products of doubles summed exactly enough in double-word),
+//      V1 = V64 (I + E)^{-1/2} = V64 (I - E/2 + 3 E^2 / 8) + O(E^3); E^2 is
+//      ~1e-30 and needs only binary64.
+//   3. A <- A V1 and V <- V1 in double-word arithmetic.
+// Only the high parts steer step 1, so its rounding never reaches the
+// result: the double-word sweeps decide convergence on A V1 itself.
+__global__ void __launch_bounds__(kDdThreads, 1)
+    k_dd_precondition(cdd* __restrict__ Aw, cdd* __restrict__ Vw, cdd* __restrict__ Sw,
+                      const DdMeta* __restrict__ meta, unsigned long long* __restrict__ flops) {
+  extern __shared__ __align__(16) unsigned char psm[];
+  double2* A64 = (double2*)psm;
+  double2* V64 = A64 + (size_t)kDdW * kDdW;
+  const int g = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int mw = meta[g].mw, nw = meta[g].nw;
+  cdd* A = Aw + (size_t)g * kDdW * kDdW;
+  cdd* V = Vw + (size_t)g * kDdW * kDdW;
+  cdd* S = Sw + (size_t)g * kDdW * kDdW;
+  __shared__ double red[kDdWarps];
+  __shared__ int rotated;
+  __shared__ unsigned long long fl;
+  double f = 0.0;
+  for (int e = tid; e < mw * nw; e += kDdThreads) {
+    const double2 a = make_double2(A[e].re.hi, A[e].im.hi);
+    A64[e] = a;
+    f += a.x * a.x + a.y * a.y;
+  }
+  for (int e = tid; e < nw * nw; e += kDdThreads) V64[e] = make_double2(e / nw == e % nw ? 1.0 : 0.0, 0.0);
+  f = warp_sum_d(f);
+  if (lane == 0) red[warp] = f;
+  if (tid == 0) fl = 0;
+  __syncthreads();
+  double frob = 0.0;
+  for (int w = 0; w < kDdWarps; ++w) frob += red[w];
+  const double tol = (double)mw * kEps64;
+  const double tiny = tol * tol * frob;
+  unsigned long long myfl = 0;
+  // ---- 1. binary64 sweeps
+  for (int sweep = 0; sweep < kDdPreSweeps; ++sweep) {
+    __syncthreads();
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < nw - 1; ++r) {
+      for (int p = warp; p < nw / 2; p += kDdWarps) {
+        int I, J;
+        dd_pair(nw, r, p, I, J);
+        double2* ap = A64 + (size_t)I * mw;
+        double2* aq = A64 + (size_t)J * mw;
+        double app = 0.0, aqq = 0.0, gx = 0.0, gy = 0.0;
+        for (int row = lane; row < mw; row += 32) {
+          const double2 x = ap[row], y = aq[row];
+          app = fma(x.x, x.x, fma(x.y, x.y, app));
+          aqq = fma(y.x, y.x, fma(y.y, y.y, aqq));
+          gx = fma(x.x, y.x, fma(x.y, y.y, gx));
+          gy = fma(x.x, y.y, fma(-x.y, y.x, gy));
+        }
+        app = warp_sum_d(app);
+        aqq = warp_sum_d(aqq);
+        gx = warp_sum_d(gx);
+        gy = warp_sum_d(gy);
+        if (lane == 0) myfl += 8ull * mw + 20;
+        if (!(app > tiny) || !(aqq > tiny)) continue;
+        const double g2 = gx * gx + gy * gy;
+        if (!(sqrt(g2) > tol * sqrt(app) * sqrt(aqq))) continue;
+        const double d = aqq - app;
+        const double sg = (d < 0.0 ? -2.0 : 2.0) / (fabs(d) + sqrt(d * d + 4.0 * g2));
+        const double tx = sg * gx, ty = sg * gy;
+        const double c = 1.0 / sqrt(1.0 + tx * tx + ty * ty);
+        const double sx = c * tx, sy = c * ty;  // s e^{i phi}
+        for (int row = lane; row < mw + nw; row += 32) {
+          double2* cp = row < mw ? ap + row : V64 + (size_t)I * nw + (row - mw);
+          double2* cq = row < mw ? aq + row : V64 + (size_t)J * nw + (row - mw);
+          const double2 x = *cp, y = *cq;
+          // x' = c x - conj(se) y ; y' = se x + c y
+          *cp = make_double2(c * x.x - (sx * y.x + sy * y.y), c * x.y - (sx * y.y - sy * y.x));
+          *cq = make_double2(fma(sx, x.x, -sy * x.y) + c * y.x, fma(sx, x.y, sy * x.x) + c * y.y);
+        }
+        if (lane == 0) {
+          rotated = 1;
+          myfl += 12ull * (mw + nw) + 20;
+        }
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (!rotated) break;
+  }
+  // ---- 2. E = V64^H V64 - I in double-word, into S (column-major, S[j nw + i] = E_ij)
+  for (int e = tid; e < nw * nw; e += kDdThreads) {
+    const int i = e % nw, j = e / nw;
+    dd re = dd_make(0.0), im = dd_make(0.0);
+    for (int k = 0; k < nw; ++k) {
+      const double2 a = V64[(size_t)i * nw + k], b = V64[(size_t)j * nw + k];
+      re = dd_add(re, dd_add(two_prod(a.x, b.x), two_prod(a.y, b.y)));
+      im = dd_add(im, dd_sub(two_prod(a.x, b.y), two_prod(a.y, b.x)));
+    }
+    if (i == j) re = dd_add_d(re, -1.0);
+    S[e] = cdd{re, im};
+  }
+  __syncthreads();
+  // E^2 (binary64, from the high parts) into the A64 area (no longer needed)
+  double2* E2 = A64;
+  for (int e = tid; e < nw * nw; e += kDdThreads) {
+    const int i = e % nw, j = e / nw;
+    double x = 0.0, y = 0.0;
+    for (int k = 0; k < nw; ++k) {
+      const cdd a = S[(size_t)k * nw + i], b = S[(size_t)j * nw + k];
+      x = fma(a.re.hi, b.re.hi, fma(-a.im.hi, b.im.hi, x));
+      y = fma(a.re.hi, b.im.hi, fma(a.im.hi, b.re.hi, y));
+    }
+    E2[e] = make_double2(x, y);
+  }
+  __syncthreads();
+  // M = I - E/2 + 3 E^2 / 8, in S
+  for (int e = tid; e < nw * nw; e += kDdThreads) {
+    const cdd s = S[e];
+    const double2 q = E2[e];
+    dd re = dd_add_d(dd{-0.5 * s.re.hi, -0.5 * s.re.lo}, 0.375 * q.x);
+    const dd im = dd_add_d(dd{-0.5 * s.im.hi, -0.5 * s.im.lo}, 0.375 * q.y);
+    if (e % nw == e / nw) re = dd_add_d(re, 1.0);
+    S[e] = cdd{re, im};
+  }
+  __syncthreads();
+  // V1 = V64 M into V
+  for (int e = tid; e < nw * nw; e += kDdThreads) {
+    const int i = e % nw, j = e / nw;
+    cdd acc = cdd_make(0.0, 0.0);
+    for (int k = 0; k < nw; ++k) {
+      const double2 a = V64[(size_t)k * nw + i];
+      const cdd m = S[(size_t)j * nw + k];
+      const dd re = dd_sub(dd_mul_d(m.re, a.x), dd_mul_d(m.im, a.y));
+      const dd im = dd_add(dd_mul_d(m.im, a.x), dd_mul_d(m.re, a.y));
+      acc = cdd_add(acc, cdd{re, im});
+    }
+    V[e] = acc;
+  }
+  __syncthreads();
+  // B = A V1 into S, then A <- B
+  for (int e = tid; e < mw * nw; e += kDdThreads) {
+    const int r = e % mw, j = e / mw;
+    cdd acc = cdd_make(0.0, 0.0);
+    for (int k = 0; k < nw; ++k) acc = cdd_add(acc, cdd_mul(A[(size_t)k * mw + r], V[(size_t)j * nw + k]));
+    S[e] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < mw * nw; e += kDdThreads) A[e] = S[e];
+  if (lane == 0 && myfl) atomicAdd(&fl, myfl);
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned long long n3 = (unsigned long long)nw * nw * nw;
+    atomicAdd(flops, fl + n3 * (4 * 2 + 4 * kFlopsDdAdd) + n3 * 8 +
+                         n3 * (4 * 6 + 4 * kFlopsDdAdd) + (unsigned long long)mw * nw * nw *
+                         (kFlopsCddMul + 2 * kFlopsDdAdd));
+  }
+}
+
 // One-sided Jacobi on the columns of A (mw x nw, column-major) with V
 // accumulated (nw x nw): the pair (p, q) is rotated while
 // |a_p^H a_q| > mw eps_dd ||a_p|| ||a_q||; columns with
@@ -177,8 +353,7 @@ __global__ void __launch_bounds__(kDdThreads, 1)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int mw = meta[g].mw, nw = meta[g].nw;
   cdd* A = Aw + (size_t)g * kDdW * kDdW;
-  cdd* V = Vw + (size_t)g * kDdW * kDdW;
-  for (int e = tid; e < nw * nw; e += kDdThreads) V[e] = cdd_make(e / nw == e % nw ? 1.0 : 0.0, 0.0);
+  cdd* V = Vw + (size_t)g * kDdW * kDdW;  // holds V1 from k_dd_precondition
   __shared__ double red[kDdWarps];
   __shared__ int rotated;
   __shared__ unsigned long long fl;
@@ -397,6 +572,7 @@ struct mps_dd_state {
   int* chi = nullptr;
   cdd* A = nullptr;
   cdd* V = nullptr;
+  cdd* S = nullptr;  // scratch of the preconditioner, one working matrix per gate
   dd* sig = nullptr;
   DdMeta* meta = nullptr;
   int* status = nullptr;
@@ -421,6 +597,7 @@ void dd_free(mps_dd_state* h) {
   cudaFree(h->chi);
   cudaFree(h->A);
   cudaFree(h->V);
+  cudaFree(h->S);
   cudaFree(h->sig);
   cudaFree(h->meta);
   cudaFree(h->status);
@@ -477,6 +654,8 @@ int dd_launch_layer(mps_dd_state* h, int k, int ng, const int* d_sites, const do
   k_dd_theta<<<ng, 256, 0, h->st>>>(h->G, h->L, h->chi, h->cap, d_sites, d_Uhi, d_Ulo, h->A, h->meta,
                                       h->counters + 1);
   DCK(cudaGetLastError());
+  k_dd_precondition<<<ng, kDdThreads, kDdPreSmem, h->st>>>(h->A, h->V, h->S, h->meta, h->counters + 1);
+  DCK(cudaGetLastError());
   k_dd_jacobi<<<ng, kDdThreads, 0, h->st>>>(h->A, h->V, h->sig, h->meta, h->max_sweeps, h->counters + 1);
   DCK(cudaGetLastError());
   k_dd_finish<<<ng, 256, 0, h->st>>>(h->G, h->L, h->chi, h->cap, h->cap, h->cutoff, h->A, h->V, h->sig, h->meta,
@@ -512,6 +691,9 @@ int mps_dd_create(int n, int chi_max, double cutoff, mps_dd_handle* out) {
   const int gmax = std::max(1, n / 2);
   A((void**)&h->A, (size_t)gmax * kDdW * kDdW * sizeof(cdd));
   A((void**)&h->V, (size_t)gmax * kDdW * kDdW * sizeof(cdd));
+  A((void**)&h->S, (size_t)gmax * kDdW * kDdW * sizeof(cdd));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_dd_precondition, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDdPreSmem);
   A((void**)&h->sig, (size_t)gmax * kDdW * sizeof(dd));
   A((void**)&h->meta, (size_t)gmax * sizeof(DdMeta));
   A((void**)&h->status, sizeof(int));
