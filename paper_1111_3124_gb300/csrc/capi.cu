@@ -597,11 +597,11 @@ int oz_gemm(mps_state* h, int ng, int kind, int M_ub, int N_ub, int K_ub, int sl
   const int sl = slices > 0 ? std::min(slices, h->slices) : h->slices;
   if (h->capturing && OzBuffers::bytes_needed(ng, M_ub, N_ub, std::min(K_ub, 512), sl) > h->oz_buf.bytes)
     return fail(MPS_ERR_CUDA, "recording: the split-GEMM buffers were sized too small");  // never reallocate mid-capture
-  launch_oz_jobs(h->d_tasks, h->d_meta, h->d_oz_jobs, ng, kind, h->stream);
+  launch_oz_jobs(h->d_tasks, h->d_meta, h->d_oz_jobs, ng, kind, sl, h->prof ? h->d_prof_flops + 3 : nullptr,
+                 h->stream);
   const int ev = pbeg(h);
   const int rc = ozaki_zgemm(h->d_oz_jobs, ng, M_ub, N_ub, K_ub, sl, h->oz_buf, h->d_oz_err, h->stream);
-  const int npair = sl * (sl + 1) / 2;
-  pend(h, 3, ev, 3, (double)ng * npair * 8.0 * M_ub * N_ub * K_ub);
+  pend(h, 3, ev, 3);  // executed flops: counted by k_oz_jobs
   h->launches_all += 1;
   if (rc == -2) return fail(MPS_ERR_NOMEM, "split GEMM buffers");
   if (rc) return fail(MPS_ERR_CUDA, "split GEMM launch failed");

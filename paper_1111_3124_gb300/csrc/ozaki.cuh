@@ -56,7 +56,11 @@ enum {
 };
 struct GateTask;
 struct TaskMeta;
-void launch_oz_jobs(const GateTask* t, const TaskMeta* m, OzJob* jobs, int ntask, int kind, cudaStream_t st);
+// Fills the job table of product `kind` (a job whose task is finished, or
+// left to the blocked sweeps, is empty); with `flops` non-null, adds the
+// tensor-core flops of the jobs that run (s slices) to it.
+void launch_oz_jobs(const GateTask* t, const TaskMeta* m, OzJob* jobs, int ntask, int kind, int s,
+                    unsigned long long* flops, cudaStream_t st);
 void launch_gate_mix2(const GateTask* t, const TaskMeta* m, int ntask, int xl_ub, int xr_ub, cudaStream_t st);
 void launch_to_f32(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
 void launch_v_to_f64(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);

@@ -32,7 +32,8 @@
 namespace mpsgb {
 
 // Fills one OzJob per task for the product `kind`.
-__global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jobs, int ntask, int kind) {
+__global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jobs, int ntask, int kind, int s,
+                          unsigned long long* flops) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ntask) return;
   const GateTask& tk = tasks[t];
@@ -170,6 +171,9 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
       break;
   }
   jobs[t] = j;
+  if (flops)  // tensor-core flops of the s(s+1)/2 slice pairs of this job (8 per complex multiply-add)
+    atomicAdd(flops, (unsigned long long)(s * (s + 1) / 2) * 8ull * (unsigned long long)j.M *
+                         (unsigned long long)j.N * (unsigned long long)j.K);
 }
 
 // theta[(i,a),(j,b)] = sum_{kl} U[(ij),(kl)] T[(k,a),(l,b)], written as the
@@ -456,8 +460,9 @@ static inline int grid_for(long long el) {
   return (int)b;
 }
 
-void launch_oz_jobs(const GateTask* t, const TaskMeta* m, OzJob* jobs, int ntask, int kind, cudaStream_t st) {
-  k_oz_jobs<<<(ntask + 127) / 128, 128, 0, st>>>(t, m, jobs, ntask, kind);
+void launch_oz_jobs(const GateTask* t, const TaskMeta* m, OzJob* jobs, int ntask, int kind, int s,
+                    unsigned long long* flops, cudaStream_t st) {
+  k_oz_jobs<<<(ntask + 127) / 128, 128, 0, st>>>(t, m, jobs, ntask, kind, s, flops);
 }
 void launch_gate_mix2(const GateTask* t, const TaskMeta* m, int ntask, int xl_ub, int xr_ub, cudaStream_t st) {
   k_gate_mix2<<<dim3(grid_for((long long)xl_ub * xr_ub), ntask), 256, 0, st>>>(t, m);
