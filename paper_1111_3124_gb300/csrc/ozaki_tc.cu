@@ -113,21 +113,49 @@ __global__ void __launch_bounds__(256) k_oz_split(const OzJob* jobs, int which, 
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   const int e = oz_exponent(mx);
   if (lane == 0) expo[(size_t)blockIdx.y * rows_cap + r] = e;
-  for (int k = lane; k < K; k += 32) {
-    const double2 x = oz_elem(v, r, k0 + k);
-    int dre[8], dim[8];
-    oz_digits(x.x, e, s, dre);
-    oz_digits(x.y, e, s, dim);
-    for (int p = 0; p < s; ++p) {
-      __nv_bfloat16* sl = base + p * slice_stride;
-      if (which == 0) {
-        sl[(size_t)(2 * r) * Kp + k] = __float2bfloat16_rn((float)dre[p]);
-        sl[(size_t)(2 * r) * Kp + K + k] = __float2bfloat16_rn((float)(-dim[p]));
-        sl[(size_t)(2 * r + 1) * Kp + k] = __float2bfloat16_rn((float)dim[p]);
-        sl[(size_t)(2 * r + 1) * Kp + K + k] = __float2bfloat16_rn((float)dre[p]);
-      } else {
-        sl[(size_t)r * Kp + k] = __float2bfloat16_rn((float)dre[p]);
-        sl[(size_t)r * Kp + K + k] = __float2bfloat16_rn((float)dim[p]);
+  if ((K & 1) == 0) {
+    // two consecutive k per lane: every slice row gets 4-byte bf16-pair stores
+    // (both halves start at even offsets because K is even)
+    for (int k = 2 * lane; k < K; k += 64) {
+      const double2 x0 = oz_elem(v, r, k0 + k), x1 = oz_elem(v, r, k0 + k + 1);
+      int r0[8], i0[8], r1[8], i1[8];
+      oz_digits(x0.x, e, s, r0);
+      oz_digits(x0.y, e, s, i0);
+      oz_digits(x1.x, e, s, r1);
+      oz_digits(x1.y, e, s, i1);
+      for (int p = 0; p < s; ++p) {
+        __nv_bfloat162* sl = reinterpret_cast<__nv_bfloat162*>(base + p * slice_stride);
+        const __nv_bfloat162 re = __floats2bfloat162_rn((float)r0[p], (float)r1[p]);
+        const __nv_bfloat162 im = __floats2bfloat162_rn((float)i0[p], (float)i1[p]);
+        if (which == 0) {
+          const __nv_bfloat162 nim = __floats2bfloat162_rn((float)(-i0[p]), (float)(-i1[p]));
+          sl[((size_t)(2 * r) * Kp + k) / 2] = re;
+          sl[((size_t)(2 * r) * Kp + K + k) / 2] = nim;
+          sl[((size_t)(2 * r + 1) * Kp + k) / 2] = im;
+          sl[((size_t)(2 * r + 1) * Kp + K + k) / 2] = re;
+        } else {
+          sl[((size_t)r * Kp + k) / 2] = re;
+          sl[((size_t)r * Kp + K + k) / 2] = im;
+        }
+      }
+    }
+  } else {
+    for (int k = lane; k < K; k += 32) {
+      const double2 x = oz_elem(v, r, k0 + k);
+      int dre[8], dim[8];
+      oz_digits(x.x, e, s, dre);
+      oz_digits(x.y, e, s, dim);
+      for (int p = 0; p < s; ++p) {
+        __nv_bfloat16* sl = base + p * slice_stride;
+        if (which == 0) {
+          sl[(size_t)(2 * r) * Kp + k] = __float2bfloat16_rn((float)dre[p]);
+          sl[(size_t)(2 * r) * Kp + K + k] = __float2bfloat16_rn((float)(-dim[p]));
+          sl[(size_t)(2 * r + 1) * Kp + k] = __float2bfloat16_rn((float)dim[p]);
+          sl[(size_t)(2 * r + 1) * Kp + K + k] = __float2bfloat16_rn((float)dre[p]);
+        } else {
+          sl[(size_t)r * Kp + k] = __float2bfloat16_rn((float)dre[p]);
+          sl[(size_t)r * Kp + K + k] = __float2bfloat16_rn((float)dim[p]);
+        }
       }
     }
   }
@@ -139,19 +167,36 @@ __global__ void __launch_bounds__(256) k_oz_split(const OzJob* jobs, int which, 
 // ------------------------------------------------------------------- GEMM ---
 
 constexpr int kOzM = 128, kOzN = 64, kOzK = 64, kOzStages = 4;
+constexpr int kOzQ = 4;  // B slices that share one A-slice tile in a pass
 constexpr int kOzABytes = kOzM * kOzK * 2, kOzBBytes = kOzN * kOzK * 2;
+constexpr int kOzStageBytes = kOzABytes + kOzQ * kOzBBytes;  // 48 KB
 constexpr int kOzThreads = 320;  // 10 warps
-constexpr int kOzSmem = kOzStages * (kOzABytes + kOzBBytes) + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int kOzTmemCols = 128;  // two 64-column fp32 accumulators
+constexpr int kOzSmem = kOzStages * kOzStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int kOzTmemCols = 512;  // two sets of kOzQ 64-column fp32 accumulators
+
+// The slice pairs (p, q), p + q < s, are taken in passes: pass (p, q0) runs
+// the pairs (p, q0 .. q0 + nq - 1), nq <= kOzQ, so that each k-tile of A's
+// slice p is loaded once for nq products (every pair in its own
+// accumulator, which keeps each fp32 sum exact). The passes alternate
+// between two accumulator sets, so that the epilogue drains one pass while
+// the tensor cores run the next.
+__device__ __forceinline__ bool oz_next_pass(int s, int& p, int& q0, int& nq) {
+  q0 += kOzQ;
+  if (q0 >= s - p) {
+    ++p;
+    q0 = 0;
+  }
+  if (p >= s) return false;
+  nq = min(kOzQ, s - p - q0);
+  return true;
+}
 
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const OzJob* jobs,
               const int* ea, const int* fb, int MpA, int NpB, int s, int* err, int k0, int kchunk) {
   extern __shared__ __align__(1024) unsigned char oz_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = smem;
-  unsigned char* sB = smem + kOzStages * kOzABytes;
-  uint64_t* bars = (uint64_t*)(sB + kOzStages * kOzBBytes);
+  uint64_t* bars = (uint64_t*)(smem + kOzStages * kOzStageBytes);
   uint64_t* full = bars;                 // [stages]
   uint64_t* empty = bars + kOzStages;    // [stages]
   uint64_t* accf = bars + 2 * kOzStages; // [2]
@@ -190,43 +235,50 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   if (warp == 0) {
     if (lane == 0) {  // ---------------------------------------------- TMA producer
       int it = 0;
-      for (int p = 0; p < s; ++p)
-        for (int q = 0; p + q < s; ++q)
-          for (int kt = 0; kt < KT; ++kt, ++it) {
-            const int st = it % kOzStages;
-            const uint32_t ph = (uint32_t)(it / kOzStages) & 1u;
-            if (!mbar_wait(&empty[st], ph ^ 1u, err)) goto producer_done;
-            mbar_expect_tx(&full[st], kOzABytes + kOzBBytes);
-            tma_load_4d(sA + st * kOzABytes, &tmA, &full[st], kt * kOzK, m0, p, blockIdx.z);
-            tma_load_4d(sB + st * kOzBBytes, &tmB, &full[st], kt * kOzK, n0, q, blockIdx.z);
-          }
+      int p = 0, q0 = -kOzQ, nq = 0;
+      while (oz_next_pass(s, p, q0, nq))
+        for (int kt = 0; kt < KT; ++kt, ++it) {
+          const int st = it % kOzStages;
+          const uint32_t ph = (uint32_t)(it / kOzStages) & 1u;
+          if (!mbar_wait(&empty[st], ph ^ 1u, err)) goto producer_done;
+          unsigned char* sa = smem + st * kOzStageBytes;
+          mbar_expect_tx(&full[st], kOzABytes + nq * kOzBBytes);
+          tma_load_4d(sa, &tmA, &full[st], kt * kOzK, m0, p, blockIdx.z);
+          for (int qi = 0; qi < nq; ++qi)
+            tma_load_4d(sa + kOzABytes + qi * kOzBBytes, &tmB, &full[st], kt * kOzK, n0, q0 + qi, blockIdx.z);
+        }
     producer_done:;
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---------------------------------------------- MMA issuer
       const uint32_t idesc = idesc_bf16_f32(kOzM, kOzN);
       int it = 0, pi = 0;
-      for (int p = 0; p < s; ++p)
-        for (int q = 0; p + q < s; ++q, ++pi) {
-          const int acc = pi & 1;
-          const uint32_t use = (uint32_t)(pi >> 1);
-          if (!mbar_wait(&acce[acc], (use & 1u) ^ 1u, err)) goto mma_done;
+      int p = 0, q0 = -kOzQ, nq = 0;
+      while (oz_next_pass(s, p, q0, nq)) {
+        const int acc = pi & 1;
+        const uint32_t use = (uint32_t)(pi >> 1);
+        if (!mbar_wait(&acce[acc], (use & 1u) ^ 1u, err)) goto mma_done;
+        tc_fence_after();
+        const uint32_t dset = tmem + (uint32_t)(acc * kOzQ * kOzN);
+        for (int kt = 0; kt < KT; ++kt, ++it) {
+          const int st = it % kOzStages;
+          const uint32_t ph = (uint32_t)(it / kOzStages) & 1u;
+          if (!mbar_wait(&full[st], ph, err)) goto mma_done;
           tc_fence_after();
-          const uint32_t dcol = tmem + (uint32_t)(acc * kOzN);
-          for (int kt = 0; kt < KT; ++kt, ++it) {
-            const int st = it % kOzStages;
-            const uint32_t ph = (uint32_t)(it / kOzStages) & 1u;
-            if (!mbar_wait(&full[st], ph, err)) goto mma_done;
-            tc_fence_after();
-            const uint64_t da = smem_desc_sw128(sA + st * kOzABytes);
-            const uint64_t db = smem_desc_sw128(sB + st * kOzBBytes);
+          unsigned char* sa = smem + st * kOzStageBytes;
+          const uint64_t da = smem_desc_sw128(sa);
+          for (int qi = 0; qi < nq; ++qi) {
+            const uint64_t db = smem_desc_sw128(sa + kOzABytes + qi * kOzBBytes);
 #pragma unroll
             for (int kk = 0; kk < kOzK / 16; ++kk)
-              mma_bf16(dcol, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, (kt | kk) != 0);
-            mma_commit(&empty[st]);
+              mma_bf16(dset + (uint32_t)(qi * kOzN), da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                       (kt | kk) != 0);
           }
-          mma_commit(&accf[acc]);
+          mma_commit(&empty[st]);
         }
+        mma_commit(&accf[acc]);
+        ++pi;
+      }
     mma_done:;
     }
   } else {  // ----------------------------------------------------------- epilogue
@@ -241,21 +293,20 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     }
     bool ok = true;
     int pi = 0;
-    for (int p = 0; p < s && ok; ++p)
-      for (int q = 0; p + q < s; ++q, ++pi) {
-        const int acc = pi & 1;
-        const uint32_t use = (uint32_t)(pi >> 1);
-        if (!mbar_wait(&accf[acc], use & 1u, err)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
+    int p = 0, q0 = -kOzQ, nq = 0;
+    while (ok && oz_next_pass(s, p, q0, nq)) {
+      const int acc = pi & 1;
+      const uint32_t use = (uint32_t)(pi >> 1);
+      if (!mbar_wait(&accf[acc], use & 1u, err)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      for (int qi = 0; qi < nq; ++qi) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(acc * kOzN + 32 * chalf), v);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&acce[acc]);
-        const int d = p + q + 2;
+        tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) +
+                      (uint32_t)(acc * kOzQ * kOzN + qi * kOzN + 32 * chalf), v);
+        const int d = p + q0 + qi + 2;
         if (d <= dh) {
           const int sh = 7 * (dh - d);
 #pragma unroll
@@ -266,6 +317,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           for (int j = 0; j < 32; ++j) lo[j] += (long long)f2i_exact(v[j]) * (1LL << sh);
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[acc]);
+      ++pi;
+    }
     if (ok) {
       const int m = m0 + 32 * quarter + lane;  // row of A^
       if (m < 2 * jb.M) {
@@ -279,7 +335,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             const int e = er + fb[(size_t)blockIdx.z * NpB + n];
             const double val = ldexp((double)hi[j], e - 7 * dh) + ldexp((double)lo[j], e - 7 * (s + 1));
             double* c = &C[2 * ((size_t)r + (size_t)n * jb.ldc) + part];
-          *c = k0 > 0 ? *c + jb.alpha * val : jb.alpha * val;  // later K chunks accumulate
+            *c = k0 > 0 ? *c + jb.alpha * val : jb.alpha * val;  // later K chunks accumulate
           }
         }
       }

@@ -306,28 +306,39 @@ __global__ void k_gram_x(const GateTask* tasks, TaskMeta* meta, int form_x) {
       const double app = tk.sigma[p], aqq = tk.sigma[q];
       const double2 g = tk.P[e];
       if (app > tiny && aqq > tiny) {
-        const double ratio = hypot(g.x, g.y) / (sqrt(app) * sqrt(aqq));
+        const double gabs = hypot(g.x, g.y);
+        const double ratio = gabs / (sqrt(app) * sqrt(aqq));
         above |= ratio > tol;
         mx = fmaxf(mx, (float)ratio);
         // the exact Jacobi angle of the pair's 2 x 2 problem, tan 2t =
         // 2 |g_pq| / (g_qq - g_pp), with g_pq's phase: exp of the resulting
         // generator is that pair's rotation (first order in the others)
         // (the small solution |t| <= pi/4 taken directly, so that an angle
-        // below pi's last bit is not lost to cancellation)
-        const double gabs = hypot(g.x, g.y);
+        // below pi's last bit is not lost to cancellation). x = g t / |g|;
+        // for z = 2|g| / |d| < 1e-2, t / |g| = (1 - z^2/3 + z^4/5 - z^6/7) / |d|
+        // (the arctangent series, relative error below z^8 / 9 < 2e-17)
+        double xa = 0.0;  // |x_pq|
         if (gabs > 0.0) {
-          const double dd = aqq - app;
-          const double t = 0.5 * atan2(2.0 * gabs, fabs(dd));
-          const double f = (dd < 0.0 ? -t : t) / gabs;
+          const double dd = aqq - app, ad = fabs(dd);
+          double f;
+          if (2.0 * gabs < 1e-2 * ad) {
+            const double inv = 1.0 / ad;
+            const double z = 2.0 * gabs * inv, z2 = z * z;
+            f = inv * fma(-z2, fma(-z2, fma(-z2, 1.0 / 7.0, 1.0 / 5.0), 1.0 / 3.0), 1.0);
+          } else {
+            f = 0.5 * atan2(2.0 * gabs, ad) / gabs;
+          }
+          if (dd < 0.0) f = -f;
           x = make_double2(g.x * f, g.y * f);
+          xa = fabs(f) * gabs;
         }
-        if (hypot(x.x, x.y) > kGramXMax) {
+        if (xa > kGramXMax) {
           // near-degenerate pair: left out of X and rotated exactly by
           // k_givens (up to kMaxGivens per task, else the blocked sweeps)
           if (ratio > tol && p < q) {
             const int slot = atomicAdd(&mt.nhard, 1);
             if (slot < kMaxGivens) {
-              const double t = hypot(x.x, x.y);
+              const double t = xa;
               const double sn = sin(t) / t;
               mt.hp[slot] = p;
               mt.hq[slot] = q;
