@@ -644,8 +644,8 @@ int run_f32_sweeps(mps_state* h, int ng, int mw_ub, int nw_ub) {
 // binary64 sweeps for what the polish leaves (split_path.cu).
 int run_split_svd(mps_state* h, int ng, int mw_ub, int nw_ub) {
   int ev = pbeg(h);
-  launch_to_f32(h->d_tasks, h->d_meta, ng, (long long)mw_ub * nw_ub + (long long)nw_ub * nw_ub, h->stream);
-  pend(h, 5, ev, 1);
+  launch_to_f32(h->d_tasks, h->d_meta, ng, nw_ub, (long long)mw_ub * nw_ub + (long long)nw_ub * nw_ub, h->stream);
+  pend(h, 5, ev, 2);
   int rc = ensure_oz(h, ng);  // its error word also serves the tensor-core rotation
   if (rc) return rc;
   rc = run_f32_sweeps(h, ng, mw_ub, nw_ub);

@@ -62,7 +62,8 @@ struct TaskMeta;
 void launch_oz_jobs(const GateTask* t, const TaskMeta* m, OzJob* jobs, int ntask, int kind, int s,
                     unsigned long long* flops, cudaStream_t st);
 void launch_gate_mix2(const GateTask* t, const TaskMeta* m, int ntask, int xl_ub, int xr_ub, cudaStream_t st);
-void launch_to_f32(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
+// Ranks the working matrix's columns by norm (k_sort_cols), then A32 = fp32(A P), V32 = P.
+void launch_to_f32(const GateTask* t, const TaskMeta* m, int ntask, int nw_ub, long long el_ub, cudaStream_t st);
 void launch_v_to_f64(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
 void launch_ns_update(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);
 void launch_take_product(const GateTask* t, TaskMeta* m, int ntask, long long el_ub, cudaStream_t st);

@@ -211,7 +211,37 @@ __global__ void __launch_bounds__(256) k_gate_mix2(const GateTask* tasks, const 
   }
 }
 
-// A32 = fp32(A), V32 = I
+// The working matrix's columns ranked by decreasing norm (ties by index),
+// into perm: the fp32 sweeps start on A P, so that columns of similar size
+// share a block and their coupling is taken by the inner solves. One CTA per
+// task; a warp per column for the norms.
+__global__ void __launch_bounds__(256) k_sort_cols(const GateTask* tasks, const TaskMeta* meta) {
+  extern __shared__ double cn[];
+  const GateTask& tk = tasks[blockIdx.x];
+  const TaskMeta& mt = meta[blockIdx.x];
+  if (mt.status) return;
+  const int Mw = mt.Mw, Nw = mt.Nw, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = warp; j < Nw; j += 8) {
+    double acc = 0.0;
+    for (int r = lane; r < Mw; r += 32) {
+      const double2 v = tk.A[(size_t)r + (size_t)j * Mw];
+      acc = fma(v.x, v.x, fma(v.y, v.y, acc));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) cn[j] = acc;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < Nw; j += blockDim.x) {
+    const double nj = cn[j];
+    int rank = 0;
+    for (int i = 0; i < Nw; ++i) rank += cn[i] > nj || (cn[i] == nj && i < j);
+    tk.perm[rank] = j;
+  }
+}
+
+// A32 = fp32(A P), V32 = P (P the permutation of k_sort_cols: column j is
+// column perm[j] of A)
 __global__ void k_to_f32(const GateTask* tasks, const TaskMeta* meta) {
   const GateTask& tk = tasks[blockIdx.y];
   const TaskMeta& mt = meta[blockIdx.y];
@@ -219,11 +249,12 @@ __global__ void k_to_f32(const GateTask* tasks, const TaskMeta* meta) {
   const size_t na = (size_t)mt.Mw * mt.Nw, nv = (size_t)mt.Nw * mt.Nw;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < na + nv; e += (size_t)gridDim.x * blockDim.x) {
     if (e < na) {
-      const double2 v = tk.A[e];
+      const size_t j = e / mt.Mw, r = e % mt.Mw;
+      const double2 v = tk.A[r + (size_t)tk.perm[j] * mt.Mw];
       tk.A32[e] = make_float2((float)v.x, (float)v.y);
     } else {
       const size_t f = e - na;
-      tk.V32[f] = make_float2((f % mt.Nw) == (f / mt.Nw) ? 1.f : 0.f, 0.f);
+      tk.V32[f] = make_float2((int)(f % mt.Nw) == tk.perm[f / mt.Nw] ? 1.f : 0.f, 0.f);
     }
   }
 }
@@ -478,7 +509,8 @@ void launch_oz_jobs(const GateTask* t, const TaskMeta* m, OzJob* jobs, int ntask
 void launch_gate_mix2(const GateTask* t, const TaskMeta* m, int ntask, int xl_ub, int xr_ub, cudaStream_t st) {
   k_gate_mix2<<<dim3(grid_for((long long)xl_ub * xr_ub), ntask), 256, 0, st>>>(t, m);
 }
-void launch_to_f32(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
+void launch_to_f32(const GateTask* t, const TaskMeta* m, int ntask, int nw_ub, long long el_ub, cudaStream_t st) {
+  k_sort_cols<<<ntask, 256, (size_t)nw_ub * sizeof(double), st>>>(t, m);
   k_to_f32<<<dim3(grid_for(el_ub), ntask), 256, 0, st>>>(t, m);
 }
 void launch_v_to_f64(const GateTask* t, const TaskMeta* m, int ntask, long long el_ub, cudaStream_t st) {
