@@ -148,6 +148,23 @@ int mps_set_tuning(mps_handle h, int n, const int* nw_max, const int* f32_block,
  * state as it was); after < 0 turns the hook off. Process-wide. */
 int mps_debug_fail_alloc(long long after);
 
+/* mps_debug_bounded_wait - test hook for the timeout path (no paper
+ * counterpart): runs, on `stream`, the bounded mbarrier wait that the
+ * tensor-core kernels use, on a barrier that nothing completes, with a limit
+ * of limit_ms (0 < limit_ms <= 10000). The wait gives up, the kernel returns
+ * with its error flag set and this call reports MPS_ERR_TIMEOUT. No copy or
+ * product is in flight when it gives up, so the context stays usable.
+ * Synchronises `stream`. Errors: MPS_ERR_ARG, MPS_ERR_NOMEM, MPS_ERR_CUDA,
+ * MPS_ERR_TIMEOUT (the expected outcome). */
+int mps_debug_bounded_wait(double limit_ms, void* stream);
+
+/* mps_debug_mark_timed_out - test hook (no paper counterpart): marks the
+ * handle as if a bounded wait of its split GEMM had run out. Every later
+ * split-precision product of the handle is refused with MPS_ERR_TIMEOUT before
+ * anything is launched, as after a real timeout (whose abandoned copies and
+ * products leave the device state untrusted). */
+int mps_debug_mark_timed_out(mps_handle h);
+
 /* mps_reset - returns the state to |0...0> (same as a fresh mps_create). */
 int mps_reset(mps_handle h);
 

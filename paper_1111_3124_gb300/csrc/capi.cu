@@ -2139,6 +2139,12 @@ int mps_debug_fail_alloc(long long after) {
   return MPS_OK;
 }
 
+int mps_debug_mark_timed_out(mps_handle h) {
+  if (!h) return fail(MPS_ERR_ARG, "null handle");
+  h->oz_timed_out = 1;  // as a bounded wait of the split GEMM that ran out would
+  return MPS_OK;
+}
+
 int mps_reset(mps_handle h) {
   if (!h) return fail(MPS_ERR_ARG, "NULL handle");
   return reset_state(h);

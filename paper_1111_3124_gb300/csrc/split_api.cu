@@ -8,6 +8,7 @@
 #include "engine.cuh"
 #include "kernels.cuh"
 #include "ozaki.cuh"
+#include "tc_ptx.cuh"
 
 using namespace mpsgb;
 
@@ -66,5 +67,45 @@ extern "C" int mps_split_zgemm(int M, int N, int K, const double* dA, long long 
     g_timed_out = true;
     return fail_msg(MPS_ERR_TIMEOUT, "split GEMM: a bounded wait ran out; the device state is not trusted");
   }
+  return MPS_OK;
+}
+
+// ---- test hook: the bounded wait of the tensor-core kernels, made to run out
+
+namespace {
+
+// One warp initialises an mbarrier that expects one arrival and then waits
+// for its first phase, which nothing completes: the wait gives up after
+// limit_ns, sets *err and the kernel returns. No copy or MMA is in flight,
+// so the context stays usable.
+__global__ void k_wait_unset_barrier(int* err, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (threadIdx.x == 0) mbar_wait_for(&bar, 0u, err, limit_ns);
+}
+
+}  // namespace
+
+extern "C" int mps_debug_bounded_wait(double limit_ms, void* stream) {
+  if (!(limit_ms > 0.0) || limit_ms > 10000.0) return fail_msg(MPS_ERR_ARG, "limit_ms must be in (0, 10000]");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* d_err = nullptr;
+  cudaError_t e = dev_alloc((void**)&d_err, sizeof(int));
+  if (e != cudaSuccess) return fail_msg(MPS_ERR_NOMEM, "mps_debug_bounded_wait: flag allocation");
+  int h_err = 0;
+  e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    k_wait_unset_barrier<<<1, 32, 0, st>>>(d_err, (unsigned long long)(limit_ms * 1e6));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_err);
+  if (e != cudaSuccess) return fail_msg(MPS_ERR_CUDA, cudaGetErrorString(e));
+  if (h_err) return fail_msg(MPS_ERR_TIMEOUT, "mps_debug_bounded_wait: the bounded wait ran out (as intended)");
   return MPS_OK;
 }

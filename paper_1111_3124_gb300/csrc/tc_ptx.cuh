@@ -42,18 +42,24 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: returns false after ~2 s without the phase completing.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+// Bounded wait: returns false after limit_ns (%globaltimer) without the
+// phase completing, or as soon as another thread has set *err; sets *err.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, int* err, uint64_t limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   while (!mbar_try(bar, parity)) {
     if (*(volatile int*)err) return false;
-    if (gtimer() - t0 > 2000000000ull) {
+    if (gtimer() - t0 > limit_ns) {
       atomicExch(err, 1);
       return false;
     }
   }
   return true;
+}
+
+// The tensor-core kernels' wait: ~2 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  return mbar_wait_for(bar, parity, err, 2000000000ull);
 }
 
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,

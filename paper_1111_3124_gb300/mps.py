@@ -42,7 +42,7 @@ EXPORTS = [
     "mps_dd_apply_layer", "mps_dd_apply_layer_device", "mps_dd_sync", "mps_dd_bond_dims", "mps_dd_get_schmidt",
     "mps_dd_amplitudes", "mps_dd_stats",
     "mps_heev_batched", "mps_hermitian_function_batched", "mps_fid_batched", "mps_dft_abs_batched",
-    "mps_hermitian_last_stats",
+    "mps_hermitian_last_stats", "mps_debug_bounded_wait", "mps_debug_mark_timed_out",
 ]
 
 
@@ -129,6 +129,8 @@ def load_library(path: str = LIB_PATH):
         "mps_fid_batched": [I, I, P, P, P, P, D, I, P, P],
         "mps_dft_abs_batched": [I, I, P, I, P, P],
         "mps_hermitian_last_stats": [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
+        "mps_debug_bounded_wait": [D, P],
+        "mps_debug_mark_timed_out": [P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -605,6 +607,17 @@ def circuit_passes(layers, owner: int = 0, device="cuda"):
             U = torch.from_numpy(np.ascontiguousarray(np.stack([_c128(u) for _, u in gs]))).to(device)
             out.append((k, [(owner, s) for s, _ in gs], U))
     return out
+
+
+def debug_bounded_wait(limit_ms: float, stream=None) -> None:
+    """Test hook: a bounded device wait on a barrier nothing completes; raises
+    MPSError(MPS_ERR_TIMEOUT) when the wait runs out, as intended."""
+    check(load_library().mps_debug_bounded_wait(float(limit_ms), _stream_ptr(stream)))
+
+
+def debug_mark_timed_out(m) -> None:
+    """Test hook: marks an MPS as if its split GEMM had timed out."""
+    check(load_library().mps_debug_mark_timed_out(m._h))
 
 
 def debug_fail_alloc(after: int) -> None:

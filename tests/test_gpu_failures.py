@@ -123,3 +123,46 @@ def test_refused_workspace_growth_keeps_state_and_held_back_gates(prec):
     ref.apply_layer(sites, np.stack(wide))
     bits = np.random.default_rng(5).integers(0, 2, size=(64, n)).astype(np.uint8)
     assert np.max(np.abs(m.amplitudes(bits) - ref.amplitudes(bits))) < 1e-13
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable():
+    """The tensor-core kernels' bounded mbarrier wait, on a barrier nothing
+    completes, gives up after its limit and reports MPS_ERR_TIMEOUT; nothing
+    was in flight, so a split-precision update right after it is unaffected."""
+    from paper_1111_3124_gb300.mps import (MPS, MPSError, MPS_ERR_TIMEOUT, PREC_SPLIT, debug_bounded_wait)
+    import time
+    t0 = time.perf_counter()
+    with pytest.raises(MPSError) as e:
+        debug_bounded_wait(5.0)
+    assert e.value.code == MPS_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    n = 8
+    layers = C.brickwork(n, 4, np.random.default_rng(31))
+    a = MPS(n, 16, 1e-12, PREC_SPLIT)
+    a.run_layers(layers)
+    b = MPS(n, 16, 1e-12)
+    b.run_layers(layers)
+    bits = np.random.default_rng(2).integers(0, 2, size=(32, n)).astype(np.uint8)
+    assert np.max(np.abs(a.amplitudes(bits) - b.amplitudes(bits))) < 1e-12
+    a.close()
+    b.close()
+
+
+def test_a_timed_out_handle_refuses_split_products_and_keeps_its_state():
+    """After a timeout of its split GEMM (marked here on the host: forcing one
+    on the GPU would abandon copies and products in flight), a handle refuses
+    every later split-precision update with MPS_ERR_TIMEOUT before launching
+    anything: its tensors stay as they were."""
+    from paper_1111_3124_gb300.mps import MPS, MPSError, MPS_ERR_TIMEOUT, PREC_SPLIT, debug_mark_timed_out
+    n = 8
+    m = MPS(n, 16, 1e-12, PREC_SPLIT)
+    m.run_layers(C.brickwork(n, 3, np.random.default_rng(32)))
+    bits = np.random.default_rng(3).integers(0, 2, size=(32, n)).astype(np.uint8)
+    before = m.amplitudes(bits)
+    debug_mark_timed_out(m)
+    for _ in range(2):
+        with pytest.raises(MPSError) as e:
+            m.apply_layer([2], C.haar_unitary(4, np.random.default_rng(4))[None])
+        assert e.value.code == MPS_ERR_TIMEOUT
+    assert np.array_equal(m.amplitudes(bits), before)
+    m.close()
