@@ -121,13 +121,13 @@ ARGS = None
 
 def workload():
     from paper_1111_3124_gb300 import circuits as C
-    c = dict(C.CONFIGS[2])
+    c = dict(C.WORKLOADS[C.N64_CHI256])
     n = ARGS.n if ARGS and ARGS.n else c["n"]
     depth = ARGS.depth if ARGS and ARGS.depth else c["depth"]
     if (n, depth) != (c["n"], c["depth"]):
         c["name"] = "n%d_d%d_u4_rz_chi%d" % (n, depth, c["chi_max"])
     c["n"], c["depth"] = n, depth
-    layers = C.config_circuit(2, n=n, depth=depth)
+    layers = C.workload_circuit(C.N64_CHI256, n=n, depth=depth)
     return c, layers, C.count_updates(layers)
 
 
@@ -340,14 +340,14 @@ def oracle_check(prec, n_updates: int):
             "case": "teacher-forced chi=256 updates of the CPU-baseline sample, GPU vs oracle"}
 
 
-def run_config3(prec, steps: int, tune_table=()):
+def run_three_site(prec, steps: int, tune_table=()):
     """Three-site workload: GHZ prefix, then a depth-12 shifted brick of Haar
     U(8) gates on n = 48, chi_max = 128, cutoff 1e-12, as one recorded program."""
     import torch
     from paper_1111_3124_gb300 import circuits as C
     from paper_1111_3124_gb300.mps import MPS, Program, circuit_passes
-    c = C.CONFIGS[3]
-    layers = C.config_circuit(3)
+    c = C.WORKLOADS[C.N48_U8]
+    layers = C.workload_circuit(C.N48_U8)
     m = MPS(c["n"], c["chi_max"], c["cutoff"], prec)
     m.set_tuning(list(tune_table))
     prog = Program([m], circuit_passes(layers))
@@ -371,7 +371,7 @@ def run_config3(prec, steps: int, tune_table=()):
     return out
 
 
-def run_config4(prec, count: int, steps: int, tune_table=()):
+def run_many_circuits(prec, count: int, steps: int, tune_table=()):
     """Many circuits at once: the first `count` circuits of the 512-circuit
     workload (n in [16, 64], depth in [8, 24], chi_max in {32, 64, 128, 256},
     Haar U(4) brickwork), recorded as one program whose passes hold the same
@@ -847,8 +847,8 @@ def run_gpu(a):
             line["oracle_check"] = {"split": oracle_check(PREC_SPLIT, a.cpu_sample),
                                     "fp64": oracle_check(PREC_FP64, a.cpu_sample)}
         if not a.no_extra_configs:
-            line["three_site"] = run_config3(prec, 2, tune_table)
-            line["many_circuits"] = run_config4(prec, a.batch_circuits, 1, tune_table)
+            line["three_site"] = run_three_site(prec, 2, tune_table)
+            line["many_circuits"] = run_many_circuits(prec, a.batch_circuits, 1, tune_table)
             line["routing"] = run_routing(prec, tune_table)
             line["double_word"] = run_dd(pk["fp64_tflops"])
             line["hermitian"] = run_hermitian(pk["fp64_tflops"])

@@ -32,8 +32,9 @@ CNOT = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=
 SWAP = np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=np.complex128)
 
 
-def rng_for(config: int, circuit: int = 0) -> np.random.Generator:
-    return np.random.default_rng(SEED_BASE + 1000 * config + circuit)
+def rng_for(group: int, circuit: int = 0) -> np.random.Generator:
+    """The generator of circuit `circuit` of a workload's seed group."""
+    return np.random.default_rng(SEED_BASE + 1000 * group + circuit)
 
 
 def haar_unitary(d: int, rng: np.random.Generator) -> np.ndarray:
@@ -104,37 +105,46 @@ def u8_shifted_brick(n: int, depth: int, rng):
     return [[(s, haar_unitary(8, rng)) for s in shifted_brick_sites(n, l)] for l in range(depth)]
 
 
-# ---------------------------------------------------------------- configs ---
+# -------------------------------------------------------------- workloads ---
 
-CONFIGS = {
-    1: dict(name="n10_d10_u4_chi32", n=10, depth=10, chi_max=32, cutoff=1e-14),
-    2: dict(name="n64_d20_u4_rz_chi256", n=64, depth=20, chi_max=256, cutoff=1e-12),
-    3: dict(name="n48_d12_u8_ghz_chi128", n=48, depth=12, chi_max=128, cutoff=1e-12),
-    4: dict(name="batch512_n16-64_d8-24_chi32-256", count=512, cutoff=1e-12),
-    5: dict(name="n96_d30_u4_chi512_sketch", n=96, depth=30, chi_max=512, cutoff=1e-10),
+# The named workloads (sizes in the names); seed_group selects their seeds.
+WORKLOADS = {
+    "n10_d10_u4_chi32": dict(name="n10_d10_u4_chi32", n=10, depth=10, chi_max=32, cutoff=1e-14, seed_group=1,
+                             kind="brickwork after a layer of U(2)"),
+    "n64_d20_u4_rz_chi256": dict(name="n64_d20_u4_rz_chi256", n=64, depth=20, chi_max=256, cutoff=1e-12,
+                                 seed_group=2, kind="brickwork with RZ phases after each layer"),
+    "n48_d12_u8_ghz_chi128": dict(name="n48_d12_u8_ghz_chi128", n=48, depth=12, chi_max=128, cutoff=1e-12,
+                                  seed_group=3, kind="GHZ prefix, then a shifted brick of U(8)"),
+    "batch512_n16-64_d8-24_chi32-256": dict(name="batch512_n16-64_d8-24_chi32-256", count=512, cutoff=1e-12,
+                                            seed_group=4, kind="512 brickwork circuits of random sizes"),
+    "n96_d30_u4_chi512_sketch": dict(name="n96_d30_u4_chi512_sketch", n=96, depth=30, chi_max=512, cutoff=1e-10,
+                                     seed_group=5, kind="brickwork"),
 }
+N10 = "n10_d10_u4_chi32"
+N64_CHI256 = "n64_d20_u4_rz_chi256"
+N48_U8 = "n48_d12_u8_ghz_chi128"
 
 
-def config_circuit(config: int, circuit: int = 0, n: int | None = None, depth: int | None = None):
+def workload_circuit(name: str, circuit: int = 0, n: int | None = None, depth: int | None = None):
     """Layers of the named workload (n, depth may be overridden for small cases)."""
-    c = CONFIGS[config]
-    rng = rng_for(config, circuit)
+    c = WORKLOADS[name]
+    rng = rng_for(c["seed_group"], circuit)
     n = c["n"] if n is None else n
     depth = c["depth"] if depth is None else depth
-    if config == 1:
+    if name == N10:
         return brickwork(n, depth, rng, first_u2_layer=True)
-    if config == 2:
+    if name == N64_CHI256:
         return brickwork(n, depth, rng, rz_after_each=True)
-    if config == 3:
+    if name == N48_U8:
         return ghz_prefix(n) + u8_shifted_brick(n, depth, rng)
-    if config == 5:
+    if name == "n96_d30_u4_chi512_sketch":
         return brickwork(n, depth, rng)
-    raise ValueError(config)
+    raise ValueError(name)
 
 
 def batch_specs(count: int = 512, circuit_seed: int = 0):
     """Per-circuit (n, depth, chi_max) of the many-circuit workload."""
-    rng = rng_for(4, circuit_seed)
+    rng = rng_for(WORKLOADS["batch512_n16-64_d8-24_chi32-256"]["seed_group"], circuit_seed)
     n = rng.integers(16, 65, size=count)
     d = rng.integers(8, 25, size=count)
     chi = rng.choice(np.array([32, 64, 128, 256]), size=count)
@@ -142,7 +152,7 @@ def batch_specs(count: int = 512, circuit_seed: int = 0):
 
 
 def batch_circuit(i: int, n: int, depth: int):
-    return brickwork(n, depth, rng_for(4, 1 + i))
+    return brickwork(n, depth, rng_for(WORKLOADS["batch512_n16-64_d8-24_chi32-256"]["seed_group"], 1 + i))
 
 
 def count_updates(layers) -> int:

@@ -43,7 +43,7 @@ def _tuning():
     return tuner.load() or []
 
 
-def config2_training_set(circuits: int, seed: int = 0, prec: int = 1):
+def chi256_training_set(circuits: int, seed: int = 0, prec: int = 1):
     """Samples logged from circuits of the shape of the chi = 256 workload
     (n = 64, depth-20 Haar U(4) brickwork with RZ phases, chi_max = 256,
     cutoff 1e-12), 630 updates each, by the split-precision full SVD."""
@@ -211,8 +211,8 @@ def main() -> None:
     from . import build as B
     B.build()
     t0 = time.perf_counter()
-    X, T = config2_training_set(a.circuits, seed=1)
-    Xv, Tv = config2_training_set(a.heldout, seed=2)
+    X, T = chi256_training_set(a.circuits, seed=1)
+    Xv, Tv = chi256_training_set(a.heldout, seed=2)
     if a.mix:
         Xm, Tm = training_set(seed=3, circuits=a.mix)
         X, T = np.concatenate([X, Xm]), np.concatenate([T, Tm])

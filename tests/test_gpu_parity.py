@@ -51,12 +51,12 @@ def test_worked_example_sec32_on_gpu():
     assert abs(rho[0, 2]) < 1e-15
 
 
-# ---------------------------------------------------------- config 1 ------
+# ------------------------------------------- n = 10 brickwork, all amplitudes ---
 
-def test_config1_all_amplitudes_vs_oracle_and_statevector():
-    c = C.CONFIGS[1]
+def test_n10_brickwork_all_amplitudes_vs_oracle_and_statevector():
+    c = C.WORKLOADS[C.N10]
     n = c["n"]
-    layers = C.config_circuit(1)
+    layers = C.workload_circuit(C.N10)
     g = gpu_mps(n, c["chi_max"], c["cutoff"])
     assert g.run_layers(layers) == 45
     ref = oracle_run(n, layers, c["chi_max"], c["cutoff"])
@@ -73,10 +73,10 @@ def test_config1_all_amplitudes_vs_oracle_and_statevector():
         assert abs(np.sum(g.schmidt(b) ** 2) - 1) < 1e-13
 
 
-def test_layer_diagnostics_no_truncation_in_config1():
-    c = C.CONFIGS[1]
+def test_layer_diagnostics_no_truncation_in_the_n10_brickwork():
+    c = C.WORKLOADS[C.N10]
     g = gpu_mps(c["n"], c["chi_max"], c["cutoff"])
-    layers = C.config_circuit(1)
+    layers = C.workload_circuit(C.N10)
     for layer in layers:
         g.run_layers([layer])
         if layer[0][1].shape[0] == 4:
@@ -122,8 +122,8 @@ def test_expectation_and_rdo_vs_oracle():
 
 # --------------------------------------------------------------- closed forms ---
 
-def test_ghz_prefix_closed_form_config3_size():
-    c = C.CONFIGS[3]
+def test_ghz_prefix_closed_form_at_n48():
+    c = C.WORKLOADS[C.N48_U8]
     n = c["n"]
     g = gpu_mps(n, c["chi_max"], c["cutoff"])
     g.run_layers(C.ghz_prefix(n))
@@ -250,7 +250,7 @@ def test_rank_deficient_theta_exact_zeros():
 
 # -------------------------------------------- full-size single updates ---
 
-def test_single_update_chi256_config2_shape():
+def test_single_update_chi256_saturated():
     """One steady-state update of the n=64, chi_max=256 workload: theta
     512 x 512 truncated to 256, on a synthetic saturated state."""
     chi = (1, 256, 256, 256, 1)
@@ -263,7 +263,7 @@ def test_single_update_chi256_config2_shape():
     assert np.max(np.abs(tg - tr)) < 1e-11 * np.max(np.abs(tr))
 
 
-def test_single_three_site_update_chi128_config3_shape():
+def test_single_three_site_update_chi128_saturated():
     chi = (1, 128, 128, 128, 128, 1)
     ref, g = single_update(chi, 128, 1, 8, 3031)
     _, rg, rl = ref.get_state()

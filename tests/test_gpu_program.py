@@ -41,11 +41,11 @@ def _oracle(n, layers, chi_max, cutoff):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_program_config1_all_amplitudes(prec):
+def test_program_n10_brickwork_all_amplitudes(prec):
     from paper_1111_3124_gb300.mps import MPS, Program, circuit_passes
-    c = C.CONFIGS[1]
+    c = C.WORKLOADS[C.N10]
     n = c["n"]
-    layers = C.config_circuit(1)
+    layers = C.workload_circuit(C.N10)
     m = MPS(n, c["chi_max"], c["cutoff"], prec)
     prog = Program([m], circuit_passes(layers))
     assert prog.updates == C.count_updates(layers)

@@ -76,10 +76,10 @@ def split_mps(n, chi_max, cutoff):
     return MPS(n, chi_max, cutoff, PREC_SPLIT)
 
 
-def test_split_config1_all_amplitudes(torch):
-    c = C.CONFIGS[1]
+def test_split_n10_brickwork_all_amplitudes(torch):
+    c = C.WORKLOADS[C.N10]
     n = c["n"]
-    layers = C.config_circuit(1)
+    layers = C.workload_circuit(C.N10)
     g = split_mps(n, c["chi_max"], c["cutoff"])
     g.run_layers(layers)
     ref = oracle_run(n, layers, c["chi_max"], c["cutoff"])

@@ -134,9 +134,9 @@ def test_mps_matches_statevector_mixed_gates(seed):
     np.testing.assert_allclose(mps_vector(mps, n), sv.vector(), atol=1e-13)
 
 
-def test_config1_all_amplitudes_no_truncation():
-    c = C.CONFIGS[1]
-    layers = C.config_circuit(1)
+def test_n10_brickwork_all_amplitudes_no_truncation():
+    c = C.WORKLOADS[C.N10]
+    layers = C.workload_circuit(C.N10)
     mps = oracle.OracleMPS(c["n"], c["chi_max"], c["cutoff"])
     sv = StateVector(c["n"])
     for layer in layers:
