@@ -135,11 +135,14 @@ int mps_set_limits(mps_handle h, int max_sweeps);
  * working-matrix width Nw (the smaller dimension of theta; no paper
  * counterpart: chosen by measurement, see the package's tuner). Entry i
  * applies to Nw <= nw_max[i] (increasing; the last entry also covers larger
- * widths): f32_block[i] = 8 or 16 columns per block, rot_tc[i] = 1 applies the
- * block rotations on the tensor cores (block width 16 only) instead of in the
- * pair kernel. n = 0 restores the default (16, pair kernel). Host arrays.
- * Errors: MPS_ERR_ARG. */
-int mps_set_tuning(mps_handle h, int n, const int* nw_max, const int* f32_block, const int* rot_tc);
+ * widths): f32_block[i] = 8 or 16 columns per block; f32_mode[i] = 0 launches
+ * one round of block pairs at a time with the rotation in the pair kernel,
+ * 1 does the same with the block rotations on the tensor cores (block width
+ * 16 only), 2 runs every sweep of every task of the pass in one scheduled
+ * launch (pairs taken in order as their inputs become final). All three
+ * compute the same rotations; 0 and 2 give identical results. n = 0 restores
+ * the default (16, mode 2). Host arrays. Errors: MPS_ERR_ARG. */
+int mps_set_tuning(mps_handle h, int n, const int* nw_max, const int* f32_block, const int* f32_mode);
 
 /* mps_debug_fail_alloc - test hook for the allocation-failure path (no paper
  * counterpart): the next `after` device or pinned-host allocations made by
@@ -393,7 +396,9 @@ int mps_program_run(mps_program_handle p);
 /* Two- and three-site updates a run of the program performs. */
 int mps_program_updates(mps_program_handle p, long long* updates);
 
-/* Releases the program (waits for handles[0]'s stream). NULL is accepted. */
+/* Releases the program after waiting for the device to finish its work. The
+ * program's handles may be destroyed before or after it (a run needs them
+ * alive). NULL is accepted. */
 int mps_program_destroy(mps_program_handle p);
 
 /* mps_sync - waits for the handle's stream and reports a deferred device

@@ -51,7 +51,10 @@ constexpr int kProfKinds = 6;  // see mps_profile in include/mps.h
 constexpr int kSplitMaxCap = kMaxCap;  // the split GEMM chunks K beyond 512
 constexpr int kF32Sweeps = 30;
 constexpr int kGramSteps = 3;  // simultaneous-rotation steps of the split path's Gram polish
-constexpr int kRotTcMinNw = 64;  // smallest working-matrix width whose fp32 rotations use the tensor cores
+// How the fp32 sweeps are launched (mps_set_tuning): one launch per round with
+// the rotation in the pair kernel, or on the tensor cores; or every sweep in
+// one scheduled launch (the default).
+constexpr int kF32ModePair = 0, kF32ModeTc = 1, kF32ModeSched = 2;
 
 // Memory budget of one batched pass: the tasks of a layer (or of many
 // circuits' layers) are processed in chunks whose workspace fits this.
@@ -98,11 +101,10 @@ struct mps_state {
   double cutoff = 0.0;
   int prec = MPS_PREC_FP64, slices = 8, svd_mode = 0;
   int max_sweeps = kMaxSweeps;  // binary64 Jacobi sweep limit (mps_set_limits)
-  int rot_tc = 0;               // fp32 sweeps rotate on the tensor cores (k_rot_tc) instead of in the pair kernel
-  // per working-matrix width: fp32 block width and rotation (mps_set_tuning);
-  // empty: block width 16, rotation in the pair kernel
+  // per working-matrix width: fp32 block width and launch mode (mps_set_tuning);
+  // empty: block width 16, all sweeps in one scheduled launch
   struct Tune {
-    int nw_max, f32_block, rot_tc;
+    int nw_max, f32_block, mode;  // mode: how the fp32 sweeps are launched (kF32Mode*)
   };
   std::vector<Tune> tune;
   // recording a program (mps_program_create): launches go into a CUDA graph,
@@ -267,7 +269,7 @@ struct TaskRef {
 // A (Mw x Nw), V (Nw x Nw, both splits of a three-site gate), T, sigma/perm,
 // and for the split-precision path A32, V32, P, Q, V2.
 struct TaskLayout {
-  size_t off[12];
+  size_t off[13];
   size_t total;
 };
 
@@ -276,7 +278,7 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 TaskLayout task_layout(const TaskRef& r, int k, bool split) {
   const mps_state* st = r.st;
   const size_t xl = st->ub[r.site], xr = st->ub[r.site + k], cap = st->cap;
-  size_t sz[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  size_t sz[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (k == 3) {
     const size_t m1 = 2 * xl, n1 = 4 * xr;
     const size_t nw1 = std::min(m1, n1), mw1 = std::max(m1, n1);
@@ -320,10 +322,11 @@ TaskLayout task_layout(const TaskRef& r, int k, bool split) {
     const size_t pairs = (nw + 31) / 32 + 1;
     sz[10] = pairs * 32 * 32 * sizeof(float2);
     sz[11] = pairs * sizeof(int);
+    sz[12] = ((nw + 7) / 8 + 2) * sizeof(int);  // per-block round counters (block width 8 or 16)
   }
   TaskLayout L;
   size_t o = 0;
-  for (int i = 0; i < 12; ++i) {
+  for (int i = 0; i < 13; ++i) {
     L.off[i] = o;
     o += align256(sz[i]);
   }
@@ -612,14 +615,28 @@ int oz_gemm(mps_state* h, int ng, int kind, int M_ub, int N_ub, int K_ub, int sl
 // tasks (the binary64 sweeps reuse the active/sweep counters).
 int run_f32_sweeps(mps_state* h, int ng, int mw_ub, int nw_ub) {
   unsigned long long* fl = h->prof ? h->d_prof_flops + 4 : nullptr;
-  // the tuned choice for this width (block width, rotation on the tensor cores)
+  // the tuned choice for this width (block width; rotation on the tensor
+  // cores, or all sweeps in one scheduled launch)
   int bw = kBlockW32;
-  bool tc = h->rot_tc && nw_ub >= kRotTcMinNw;
+  int mode = kF32ModeSched;
   for (const mps_state::Tune& t : h->tune) {
     bw = t.f32_block;
-    tc = t.rot_tc != 0;
+    mode = t.mode;
     if (nw_ub <= t.nw_max) break;
   }
+  if (mode == kF32ModeSched) {
+    const int ev = pbeg(h);
+    const int nl = launch_jacobi_f32_sched(h->d_tasks, h->d_meta, ng, nw_ub, bw, kF32Sweeps, h->d_counter + 4,
+                                           h->d_oz_err, fl, h->stream);
+    if (nl < 0) {
+      const cudaError_t e = cudaGetLastError();
+      return fail(MPS_ERR_CUDA, std::string("scheduled fp32 sweeps: ") + cudaGetErrorString(e));
+    }
+    pend(h, 4, ev, nl);
+    CK(cudaGetLastError());
+    return MPS_OK;
+  }
+  const bool tc = mode == kF32ModeTc;
   const int nb = (nw_ub + bw - 1) / bw;
   const int nbe = nb + (nb & 1);
   return device_loop(h, kF32Sweeps, true, [&]() -> int {
@@ -797,6 +814,7 @@ size_t build_tasks(mps_state* w, int k, const std::vector<TaskRef>& refs, const 
     t.V2 = reinterpret_cast<double2*>(tb + o[9]);
     t.Wp = reinterpret_cast<float2*>(tb + o[10]);
     t.Wneed = reinterpret_cast<int*>(tb + o[11]);
+    t.qver = reinterpret_cast<int*>(tb + o[12]);
     out[g] = t;
   }
   (void)w;
@@ -1755,7 +1773,9 @@ constexpr int kProgMaxTasks = 512;  // gate tasks per recorded pass (bounds the 
 
 void free_program(mps_program* p) {
   if (!p) return;
-  if (!p->hs.empty() && p->hs[0]->stream) cudaStreamSynchronize(p->hs[0]->stream);
+  // the handles may already be destroyed (their stream with them): wait for
+  // the whole device rather than touch them
+  cudaDeviceSynchronize();
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->graph) cudaGraphDestroy(p->graph);
   cudaFree(p->mem);
@@ -2077,8 +2097,9 @@ int mps_create(int n, int chi_max, double cutoff, mps_handle* out) {
   if ((e = dev_alloc((void**)&h->gamma, sizeof(double2) * gamma_elems(h))) != cudaSuccess) return bad(e);
   if ((e = dev_alloc((void**)&h->lambda, sizeof(double) * (size_t)(n + 1) * chi_max)) != cudaSuccess) return bad(e);
   if ((e = dev_alloc((void**)&h->chi, sizeof(int) * (n + 1))) != cudaSuccess) return bad(e);
-  if ((e = dev_alloc((void**)&h->d_counter, 4 * sizeof(int))) != cudaSuccess) return bad(e);
-  if ((e = cudaMemset(h->d_counter, 0, 4 * sizeof(int))) != cudaSuccess) return bad(e);
+  // words 0-2: active count, sticky status, loop iteration; 4-7: the scheduled fp32 sweeps' counters
+  if ((e = dev_alloc((void**)&h->d_counter, 8 * sizeof(int))) != cudaSuccess) return bad(e);
+  if ((e = cudaMemset(h->d_counter, 0, 8 * sizeof(int))) != cudaSuccess) return bad(e);
   if ((e = host_alloc((void**)&h->h_counter, sizeof(int))) != cudaSuccess) return bad(e);
   int rc = reset_state(h);
   if (rc) { free_state(h); return rc; }
@@ -2119,15 +2140,17 @@ int mps_set_limits(mps_handle h, int max_sweeps) {
   return MPS_OK;
 }
 
-int mps_set_tuning(mps_handle h, int n, const int* nw_max, const int* f32_block, const int* rot_tc) {
+int mps_set_tuning(mps_handle h, int n, const int* nw_max, const int* f32_block, const int* f32_mode) {
   if (!h) return fail(MPS_ERR_ARG, "NULL handle");
-  if (n < 0 || (n > 0 && (!nw_max || !f32_block || !rot_tc))) return fail(MPS_ERR_ARG, "bad table");
+  if (n < 0 || (n > 0 && (!nw_max || !f32_block || !f32_mode))) return fail(MPS_ERR_ARG, "bad table");
   std::vector<mps_state::Tune> t(n);
   for (int i = 0; i < n; ++i) {
     if (f32_block[i] != 8 && f32_block[i] != 16) return fail(MPS_ERR_ARG, "fp32 block width must be 8 or 16");
-    if (rot_tc[i] && f32_block[i] != 16) return fail(MPS_ERR_ARG, "the tensor-core rotation needs block width 16");
+    if (f32_mode[i] < kF32ModePair || f32_mode[i] > kF32ModeSched) return fail(MPS_ERR_ARG, "fp32 mode must be 0, 1 or 2");
+    if (f32_mode[i] == kF32ModeTc && f32_block[i] != 16)
+      return fail(MPS_ERR_ARG, "the tensor-core rotation needs block width 16");
     if (i > 0 && nw_max[i] <= nw_max[i - 1]) return fail(MPS_ERR_ARG, "widths must increase");
-    t[i] = mps_state::Tune{nw_max[i], f32_block[i], rot_tc[i] ? 1 : 0};
+    t[i] = mps_state::Tune{nw_max[i], f32_block[i], f32_mode[i]};
   }
   CK(cudaStreamSynchronize(h->stream));
   h->tune = t;

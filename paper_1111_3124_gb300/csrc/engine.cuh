@@ -49,6 +49,7 @@ struct GateTask {
   double2* V2;          // Nw x Nw scratch: X^3, then the column scales of A W
   float2* Wp;           // fp32 sweeps: each block pair's 32 x 32 rotation W (for the tensor-core rotation)
   int* Wneed;           //   and whether that pair rotated in this round
+  int* qver;            // scheduled fp32 sweeps: rounds finished on each block (nb + 1 entries)
 };
 
 // Per-task state written and read by kernels only.
@@ -73,6 +74,8 @@ struct TaskMeta {
   double kept_norm;     // sqrt(sum of kept sigma^2) of the current split
   double frob2;         // ||A||_F^2 of the current working matrix
   unsigned int maxoff;  // float bits: largest |g_pq|/sqrt(g_pp g_qq) seen in this sweep
+  int q_done;           // scheduled fp32 sweeps: block pairs finished (all sweeps)
+  int q_sweep;          //   sweeps whose end-of-sweep decision is published
 };
 
 // Readout / single-site tasks.

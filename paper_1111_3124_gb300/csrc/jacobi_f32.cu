@@ -29,6 +29,8 @@
 // The binary64 sweeps that follow (Gram polish, blocked binary64 Jacobi) make
 // the binary64 orthogonality test, so this stage only has to bring the
 // columns close to orthogonal.
+#include <algorithm>
+
 #include "engine.cuh"
 #include "kernels.cuh"
 
@@ -137,12 +139,19 @@ struct JacobiSmem {
 
 }  // namespace
 
+// Columns of A32 and V32 are read at L2 (ld.global.cg): under the scheduled
+// launch below, other CTAs of the same launch wrote them.
+__device__ __forceinline__ float2 ld_col(const float2* p) { return __ldcg(p); }
+
+// One block pair (I, J) of task `task` in round `round`: steps 1-4 above.
 // FUSED: the CTA rotates the columns of A32 and V32 itself (step 4 below).
 // Otherwise it writes W (and whether the pair rotated) to the task's Wp /
-// Wneed, and k_rot_tc applies W on the tensor cores.
+// Wneed, and k_rot_tc applies W on the tensor cores. Every early return is
+// taken by the whole CTA. make_prs: fill the inner pairing table (it depends
+// only on BW, so a CTA that runs several pairs fills it once).
 template <int BW, bool FUSED>
-__global__ void __launch_bounds__(256, 3)
-    k_jacobi_pair_f32(const GateTask* tasks, TaskMeta* meta, int round, unsigned long long* flops) {
+__device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, int task, int round, int pair,
+                                         unsigned long long* flops, unsigned char* jsm_raw, bool make_prs) {
   constexpr int C2 = 2 * BW;                // columns of a block pair
   constexpr int NP = C2 / 2;                // disjoint rotations per inner round
   constexpr int RCH = kRch;
@@ -160,20 +169,19 @@ __global__ void __launch_bounds__(256, 3)
   static_assert(NPART >= 1, "Gram tiling");
   static_assert(NP * NP % 32 == 0 && NP <= 32, "2 x 2 blocks fill whole warps");
 
-  TaskMeta& mt = meta[blockIdx.y];
+  TaskMeta& mt = meta[task];
   if (!mt.active) return;
-  const GateTask& tk = tasks[blockIdx.y];
+  const GateTask& tk = tasks[task];
   const int Mw = mt.Mw, Nw = mt.Nw;
   const int nb = (Nw + BW - 1) / BW;
   const int nbe = nb + (nb & 1);
-  if (round >= nbe - 1 || (int)blockIdx.x >= nbe / 2) return;
+  if (round >= nbe - 1 || pair >= nbe / 2) return;
   int I, J;
-  rr_pair_f(nbe, round, blockIdx.x, I, J);
+  rr_pair_f(nbe, round, pair, I, J);
   float2* const A = tk.A32;
   float2* const Vm = tk.V32;
   const float2 zero = make_float2(0.f, 0.f);
 
-  extern __shared__ __align__(16) unsigned char jsm_raw[];
   JacobiSmem<BW>& S = *reinterpret_cast<JacobiSmem<BW>*>(jsm_raw);
   int* const cols = S.cols;
   auto& buf = S.buf;
@@ -189,7 +197,7 @@ __global__ void __launch_bounds__(256, 3)
     const int j = blk * BW + (tid % BW);
     cols[tid] = (blk < nb && j < Nw) ? j : -1;
   }
-  for (int e = tid; e < (C2 - 1) * NP; e += 256) {
+  for (int e = tid; make_prs && e < (C2 - 1) * NP; e += 256) {
     int p, q;
     rr_pair_f(C2, e / NP, e % NP, p, q);
     prs[e / NP][e % NP][0] = (unsigned char)p;
@@ -209,7 +217,7 @@ __global__ void __launch_bounds__(256, 3)
     for (int j = 0; j < PER; ++j) {
       const int e = tid + 256 * j, col = e / RCH, row = e % RCH;
       const int gc = cols[col];
-      pf[j] = (gc >= 0 && r0 + row < rows) ? M[(size_t)(r0 + row) + (size_t)gc * rows] : zero;
+      pf[j] = (gc >= 0 && r0 + row < rows) ? ld_col(&M[(size_t)(r0 + row) + (size_t)gc * rows]) : zero;
     }
   };
   auto stash = [&](int b) {
@@ -316,7 +324,7 @@ __global__ void __launch_bounds__(256, 3)
   if (!need) {
     if (tid == 0) {
       if (flops) atomicAdd(flops, 4ull * nv * (nv + 1) * (unsigned long long)Mw);
-      if (!FUSED) tk.Wneed[blockIdx.x] = 0;
+      if (!FUSED) tk.Wneed[pair] = 0;
     }
     return;
   }
@@ -391,10 +399,10 @@ __global__ void __launch_bounds__(256, 3)
   }
 
   if (!FUSED) {  // hand W to the tensor-core rotation
-    float2* Wo = tk.Wp + (size_t)blockIdx.x * C2 * C2;
+    float2* Wo = tk.Wp + (size_t)pair * C2 * C2;
     for (int e = tid; e < C2 * C2; e += 256) Wo[e] = W[e / C2][e % C2];
     if (tid == 0) {
-      tk.Wneed[blockIdx.x] = 1;
+      tk.Wneed[pair] = 1;
       mt.rotated = 1;
       if (flops)
         atomicAdd(flops, 4ull * nv * (nv + 1) * (unsigned long long)Mw + 60ull * C2 * (unsigned long long)nrot +
@@ -459,6 +467,194 @@ __global__ void __launch_bounds__(256, 3)
   }
 }
 
+// One launch per round-robin round: blockIdx.y = task, blockIdx.x = pair.
+template <int BW, bool FUSED>
+__global__ void __launch_bounds__(256, 3)
+    k_jacobi_pair_f32(const GateTask* tasks, TaskMeta* meta, int round, unsigned long long* flops) {
+  extern __shared__ __align__(16) unsigned char jsm_raw[];
+  pair_f32<BW, FUSED>(tasks, meta, blockIdx.y, round, blockIdx.x, flops, jsm_raw, true);
+}
+
+// ---- Scheduled sweeps: every fp32 sweep of every task in one launch
+//
+// The work items (sweep s, round r, task t, pair p) are numbered sweep-major,
+// then by round, task and pair. A CTA takes the next number from a counter,
+// waits until the item's inputs are final, runs the pair (steps 1-4) and
+// reports it. An item depends on the two items of the previous round of its
+// own task that last wrote its blocks I and J (per-block round counters,
+// qver) and, in the first round of a sweep, on the decision taken at the end
+// of the task's previous sweep. The
+// numbering is a topological order of these dependencies and a CTA takes an
+// item only while it runs, so the unfinished item with the smallest number
+// always has its inputs ready and every wait ends. Each wait is bounded all
+// the same (kSchedWaitNs by %globaltimer): one that runs out sets the error
+// word and every CTA of the launch returns.
+//
+// Per task, q_done counts the finished pairs of all its sweeps. The CTA that
+// finishes the last pair of a sweep takes the end-of-sweep decision (the task
+// stops when no pair rotated, or at the sweep limit) and then publishes it in
+// q_sweep: the next sweep's number, or kSweepStopped, which ends the wait of
+// any later item of the task (such items are skipped). Tasks that do not
+// sweep at all start at kSweepStopped. Each task runs the pairs, rounds and sweeps of the per-round
+// launches on the same data, so the results are the same bit for bit; only
+// the order in which independent pairs run differs. What this removes is the
+// launch per round and the partly filled last wave of every round (a
+// saturated round of 32 tasks is 512 CTAs against 456 resident).
+struct F32Sched {
+  unsigned long long head;  // next work item
+  int n_active;             // tasks still sweeping
+  int pad;
+};
+static_assert(sizeof(F32Sched) <= 16, "fits the handle's counter words 4..7");
+
+constexpr unsigned long long kSchedWaitNs = 2000000000ull;
+// q_sweep of a task that no longer sweeps: above every sweep number, so that
+// a wait on any later sweep of that task ends at once (the item is then skipped)
+constexpr int kSweepStopped = 1 << 30;
+
+namespace {
+
+__device__ __forceinline__ unsigned long long sched_clock_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int add_acq_rel_gpu(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// Thread 0 of a CTA: waits until *p >= v. false: the error word is set (this
+// wait ran out, or another CTA's did).
+__device__ bool wait_at_least(const int* p, int v, int* err) {
+  if (ld_acquire_gpu(p) >= v) return true;
+  const unsigned long long t0 = sched_clock_ns();
+  for (;;) {
+    __nanosleep(256);
+    if (ld_acquire_gpu(p) >= v) return true;
+    if (*(volatile int*)err) return false;
+    if (sched_clock_ns() - t0 > kSchedWaitNs) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+}
+
+}  // namespace
+
+// One CTA per task: resets its counters and counts it if it sweeps (the
+// launcher zeroes the F32Sched words first).
+template <int BW>
+__global__ void k_f32_sched_setup(const GateTask* tasks, TaskMeta* meta, F32Sched* q) {
+  TaskMeta& mt = meta[blockIdx.x];
+  const int nb = (mt.Nw + BW - 1) / BW, nbe = nb + (nb & 1);
+  int* ver = tasks[blockIdx.x].qver;
+  for (int b = threadIdx.x; b < nbe; b += blockDim.x) ver[b] = 0;
+  if (threadIdx.x == 0) {
+    mt.q_done = 0;
+    if (mt.active && mt.Nw < 1) {  // no pair: one empty sweep, as the per-round launches
+      mt.sweeps += 1;
+      mt.sweeps_total += 1;
+      mt.active = 0;
+      mt.rotated = 0;
+      mt.maxoff = 0u;
+    }
+    mt.q_sweep = mt.active ? 0 : kSweepStopped;
+    if (mt.active) atomicAdd(&q->n_active, 1);
+  }
+}
+
+template <int BW>
+__global__ void __launch_bounds__(256, 3)
+    k_jacobi_f32_sched(const GateTask* tasks, TaskMeta* meta, int ntask, int r_ub, int p_ub, int max_sweeps,
+                       unsigned long long total, F32Sched* q, int* err, unsigned long long* flops) {
+  extern __shared__ __align__(16) unsigned char jsm_raw[];
+  __shared__ int item[4];  // task (-1: nothing left), round, pair, sweep
+  {
+    JacobiSmem<BW>& S = *reinterpret_cast<JacobiSmem<BW>*>(jsm_raw);
+    constexpr int C2 = 2 * BW, NP = BW;
+    for (int e = threadIdx.x; e < (C2 - 1) * NP; e += blockDim.x) {
+      int p, qq;
+      rr_pair_f(C2, e / NP, e % NP, p, qq);
+      S.prs[e / NP][e % NP][0] = (unsigned char)p;
+      S.prs[e / NP][e % NP][1] = (unsigned char)qq;
+    }
+  }
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int t = -1, r = 0, p = 0, s = 0;
+      for (;;) {
+        t = -1;
+        if (*(volatile int*)&q->n_active == 0 || *(volatile int*)err) break;
+        const unsigned long long w = atomicAdd(&q->head, 1ull);
+        if (w >= total) break;
+        unsigned long long x = w;
+        p = (int)(x % (unsigned)p_ub);
+        x /= (unsigned)p_ub;
+        const int tt = (int)(x % (unsigned)ntask);
+        x /= (unsigned)ntask;
+        r = (int)(x % (unsigned)r_ub);
+        s = (int)(x / (unsigned)r_ub);
+        TaskMeta& mt = meta[tt];
+        const int nb = (mt.Nw + BW - 1) / BW, nbe = nb + (nb & 1);
+        const int nr = nbe - 1, np = nbe / 2;
+        if (r >= nr || p >= np) continue;  // the task has fewer blocks
+        if (!wait_at_least(&mt.q_sweep, s, err)) break;
+        if (!*(volatile int*)&mt.active) continue;  // stopped at the end of an earlier sweep
+        if (r > 0) {  // the round before wrote blocks I and J
+          int I, J;
+          rr_pair_f(nbe, r, p, I, J);
+          const int* ver = tasks[tt].qver;
+          if (!wait_at_least(ver + I, s * nr + r, err) || !wait_at_least(ver + J, s * nr + r, err)) break;
+        }
+        t = tt;
+        break;
+      }
+      item[0] = t;
+      item[1] = r;
+      item[2] = p;
+      item[3] = s;
+    }
+    __syncthreads();
+    const int t = item[0], r = item[1], p = item[2], s = item[3];
+    if (t < 0) return;
+    pair_f32<BW, true>(tasks, meta, t, r, p, flops, jsm_raw, false);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      TaskMeta& mt = meta[t];
+      const int nb = (mt.Nw + BW - 1) / BW, nbe = nb + (nb & 1);
+      const int nr = nbe - 1, per_sweep = nr * (nbe / 2);
+      int I, J;
+      rr_pair_f(nbe, r, p, I, J);
+      int* ver = tasks[t].qver;
+      __threadfence();
+      st_release_gpu(ver + I, s * nr + r + 1);
+      st_release_gpu(ver + J, s * nr + r + 1);
+      if (add_acq_rel_gpu(&mt.q_done, 1) + 1 == (s + 1) * per_sweep) {
+        // end of the task's sweep s (the end-of-sweep rule without a failure at the limit)
+        mt.sweeps += 1;
+        mt.sweeps_total += 1;
+        mt.maxoff = 0u;
+        const bool stop = !mt.rotated || mt.sweeps >= max_sweeps;
+        if (stop) mt.active = 0;
+        mt.rotated = 0;
+        __threadfence();
+        st_release_gpu(&mt.q_sweep, stop ? kSweepStopped : s + 1);
+        if (stop) atomicSub(&q->n_active, 1);
+      }
+    }
+  }
+}
+
 template <int BW, bool FUSED>
 static void launch_pair_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub,
                             unsigned long long* flops, cudaStream_t st) {
@@ -466,9 +662,22 @@ static void launch_pair_f32(const GateTask* t, TaskMeta* m, int ntask, int round
   k_jacobi_pair_f32<BW, FUSED><<<dim3(pairs_ub, ntask), 256, bytes, st>>>(t, m, round, flops);
 }
 
+static int g_sched_ctas[2] = {0, 0};  // resident CTAs of the scheduled kernel (block width 8, 16)
+
 void jacobi_f32_prepare() {
   static bool done = false;
   if (done) return;
+  cudaFuncSetAttribute(k_jacobi_f32_sched<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(JacobiSmem<8>));
+  cudaFuncSetAttribute(k_jacobi_f32_sched<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(JacobiSmem<16>));
+  int dev = 0, sms = 0, per8 = 0, per16 = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per8, k_jacobi_f32_sched<8>, 256, sizeof(JacobiSmem<8>));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per16, k_jacobi_f32_sched<16>, 256, sizeof(JacobiSmem<16>));
+  g_sched_ctas[0] = std::max(1, per8) * std::max(1, sms);
+  g_sched_ctas[1] = std::max(1, per16) * std::max(1, sms);
   cudaFuncSetAttribute(k_jacobi_pair_f32<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sizeof(JacobiSmem<8>));
   cudaFuncSetAttribute(k_jacobi_pair_f32<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -487,6 +696,43 @@ void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int roun
     launch_pair_f32<16, true>(t, m, ntask, round, pairs_ub, flops, st);
   else
     launch_pair_f32<16, false>(t, m, ntask, round, pairs_ub, flops, st);
+}
+
+// All fp32 sweeps of every task in one scheduled launch (fused rotation),
+// after a set-up of the counters (one CTA per task). sched points to four ints of device
+// memory (8-byte aligned) the launch may overwrite; err is the handle's error
+// word. Returns the number of launches (0 or 2), or -1 when the launch failed.
+int launch_jacobi_f32_sched(const GateTask* t, TaskMeta* m, int ntask, int nw_ub, int bw, int max_sweeps,
+                            void* sched, int* err, unsigned long long* flops, cudaStream_t st) {
+  jacobi_f32_prepare();
+  if (ntask < 1 || nw_ub < 1 || max_sweeps < 1) return 0;
+  const int nb = (nw_ub + bw - 1) / bw, nbe = nb + (nb & 1);
+  const int r_ub = nbe - 1, p_ub = nbe / 2;
+  const unsigned long long total = (unsigned long long)max_sweeps * r_ub * (unsigned long long)ntask * p_ub;
+  F32Sched* q = static_cast<F32Sched*>(sched);
+  if (cudaMemsetAsync(q, 0, sizeof(F32Sched), st) != cudaSuccess) return -1;
+  if (bw == 8)
+    k_f32_sched_setup<8><<<ntask, 128, 0, st>>>(t, m, q);
+  else
+    k_f32_sched_setup<16><<<ntask, 128, 0, st>>>(t, m, q);
+  const unsigned long long cap = (unsigned long long)g_sched_ctas[bw == 8 ? 0 : 1];
+  // a cooperative launch (every CTA resident at once); the pull order above
+  // needs only that a CTA holding an item runs, which any launch gives
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)std::min(total, cap));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = bw == 8 ? sizeof(JacobiSmem<8>) : sizeof(JacobiSmem<16>);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = bw == 8 ? cudaLaunchKernelEx(&cfg, k_jacobi_f32_sched<8>, t, m, ntask, r_ub, p_ub, max_sweeps,
+                                                     total, q, err, flops)
+                                : cudaLaunchKernelEx(&cfg, k_jacobi_f32_sched<16>, t, m, ntask, r_ub, p_ub, max_sweeps,
+                                                     total, q, err, flops);
+  return e == cudaSuccess ? 2 : -1;
 }
 
 }  // namespace mpsgb

@@ -4,8 +4,9 @@ For each bucket of working-matrix widths Nw (the smaller dimension of theta,
 2 chi at saturation), times one brickwork layer of Haar U(4) updates on a
 synthetic state of 64 sites whose bonds sit at chi = Nw / 2 (where the
 chain's ends allow), once per candidate launch
-shape (fp32 block width 8 or 16; block rotations in the pair kernel or on the
-tensor cores), and keeps the fastest. The table is cached as JSON and applied
+shape (fp32 block width 8 or 16; one launch per round with the block
+rotations in the pair kernel or on the tensor cores, or every sweep in one
+scheduled launch), and keeps the fastest. The table is cached as JSON and applied
 to handles with MPS.set_tuning; nothing here computes any part of the update.
 
   python -m paper_1111_3124_gb300.tuner [--out PATH] [--chis 32 64 128 256]
@@ -18,7 +19,11 @@ import time
 
 import numpy as np
 
-CANDIDATES = [(16, 0), (8, 0), (16, 1)]  # (fp32 block width, rotation on the tensor cores)
+# (fp32 block width, launch mode): 0 one launch per round, rotation in the
+# pair kernel; 1 the same with the rotation on the tensor cores; 2 every sweep
+# in one scheduled launch
+CANDIDATES = [(16, 2), (8, 2), (16, 0), (8, 0), (16, 1)]
+MODE_NAMES = {0: "round", 1: "tc", 2: "sched"}
 DEFAULT_CHIS = (32, 64, 128, 256)
 
 
@@ -51,7 +56,7 @@ def _layer_time(chi: int, cand, n: int, reps: int) -> float:
 
 
 def tune(chis=DEFAULT_CHIS, reps: int = 3, n: int = 64):
-    """Returns (table, measurements): table rows (nw_max, f32_block, rot_tc).
+    """Returns (table, measurements): table rows (nw_max, f32_block, mode).
     n = 64 sites give a layer of about 30 concurrent updates, most of them
     saturated, as in the circuits the table serves."""
     table, meas = [], {}
@@ -59,7 +64,7 @@ def tune(chis=DEFAULT_CHIS, reps: int = 3, n: int = 64):
         times = {cand: _layer_time(chi, cand, n, reps) for cand in CANDIDATES}
         best = min(times, key=times.get)
         table.append((2 * chi, best[0], best[1]))
-        meas[str(2 * chi)] = {"%d/%s" % (c[0], "tc" if c[1] else "fused"): t for c, t in times.items()}
+        meas[str(2 * chi)] = {"%d/%s" % (c[0], MODE_NAMES[c[1]]): t for c, t in times.items()}
     return table, meas
 
 
