@@ -768,7 +768,7 @@ def run_gpu(a):
             derived % (2, pk["sm_mhz"])),
         1: ("k_contract (theta, binary64)", "alu", pk["fp64_tflops"], derived % (2, pk["sm_mhz"])),
         3: ("k_oz_gemm (split-precision bf16 tcgen05 GEMM)", "tensor", pk["bf16_tflops"], pk["bf16_source"]),
-        4: ("k_jacobi_pair_f32<16> (fp32 preconditioning sweeps)", "alu", pk["fp32_tflops"],
+        4: (f32_kernel_name(tune_table, 2 * c["chi_max"]), "alu", pk["fp32_tflops"],
             derived % (128, pk["sm_mhz"])),
     }
     dom = max(roof_def, key=lambda i: prof[i]["ms"])
@@ -787,8 +787,10 @@ def run_gpu(a):
         algorithmic = "tensor-core flops of the slice products"
     # DRAM bytes per launch from one ncu capture of a saturated chi=256 layer
     # (the --profile-layer case), scaled to this run's average launch by
-    # duration (both Jacobi kernels are ALU-bound: time tracks work)
-    captured = {0: (390.9e6, 2.2237), 4: (146.0e6, 0.1697)}  # class -> (bytes, ms) per launch
+    # duration (the Jacobi kernels are ALU-bound: time tracks work)
+    captured = {0: (390.9e6, 2.2237)}
+    if f32_mode(tune_table, 2 * c["chi_max"])[1] in F32_CAPTURED:
+        captured[4] = F32_CAPTURED[f32_mode(tune_table, 2 * c["chi_max"])[1]]
     ms_launch = d["ms"] / max(d["launches"], 1)
     traffic = captured[dom][0] * ms_launch / captured[dom][1] if dom in captured else None
     roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -817,7 +819,8 @@ def run_gpu(a):
                        else "eager (host-driven passes)",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MiB buffer written between timed steps; working set > L2",
-                       "tuning": {"table (nw_max, fp32 block, rotation on tensor cores)": tune_table,
+                       "tuning": {"table (nw_max, fp32 block, launch mode: 0 per round, 1 tensor-core rotation, "
+                                  "2 scheduled)": tune_table,
                                   "source": tune_source},
                        "max_bond": int(max(chi)) if len(chi) else 1},
             "roofline": roof, "kernels": kernels, "clocks": clocks,
@@ -859,6 +862,31 @@ def run_gpu(a):
     m.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+# fp32 sweeps: DRAM read + write bytes and duration of one captured launch of
+# the saturated chi=256 layer (--profile-layer), per launch mode
+F32_CAPTURED = {0: (146.0e6, 0.1697), 2: (42.16e9, 60.91)}
+
+
+def f32_mode(tune_table, nw):
+    """(block width, launch mode) the tuning table gives the fp32 sweeps at
+    width nw (the library's default without a table: 16, scheduled)."""
+    bw, mode = 16, 2
+    for nw_max, b, md in (tune_table or []):
+        bw, mode = b, md
+        if nw <= nw_max:
+            break
+    return bw, mode
+
+
+def f32_kernel_name(tune_table, nw):
+    bw, mode = f32_mode(tune_table, nw)
+    if mode == 2:
+        return "k_jacobi_f32_sched<%d> (fp32 preconditioning sweeps, one scheduled launch per pass)" % bw
+    if mode == 1:
+        return "k_jacobi_pair_f32<16> + k_rot_tc (fp32 preconditioning sweeps, tensor-core rotation)"
+    return "k_jacobi_pair_f32<%d> (fp32 preconditioning sweeps, one launch per round)" % bw
 
 
 def run_profile_layer(a):

@@ -19,9 +19,10 @@
 // 64-bit integers per output (diagonals p+q <= 5 and > 5, shifted), and
 // converts them to binary64 once, with the scales 2^{e_r + f_n}.
 // Pipeline. One CTA per 128 x 64 output tile of A^ B^T: warp 0 issues TMA
-// loads (SWIZZLE_128B, 4 stages), warp 1 issues the MMAs (M = 128, N = 64,
-// K = 16 per instruction) alternating between two TMEM accumulators, warps
-// 2..9 drain an accumulator while the next pair is being multiplied. Every
+// loads (SWIZZLE_128B, 4 stages), warp 1 issues the MMAs (M = 128, K = 16
+// per instruction, N = 64 per slice pair of a pass: up to four pairs in one
+// instruction of N = 256) alternating between two TMEM accumulator sets,
+// warps 2..9 drain a set while the next pass is being multiplied. Every
 // wait is bounded (%globaltimer); a timeout sets an error flag and the CTA
 // returns after releasing its TMEM.
 #include <cuda.h>
@@ -251,7 +252,6 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---------------------------------------------- MMA issuer
-      const uint32_t idesc = idesc_bf16_f32(kOzM, kOzN);
       int it = 0, pi = 0;
       int p = 0, q0 = -kOzQ, nq = 0;
       while (oz_next_pass(s, p, q0, nq)) {
@@ -260,6 +260,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         if (!mbar_wait(&acce[acc], (use & 1u) ^ 1u, err)) goto mma_done;
         tc_fence_after();
         const uint32_t dset = tmem + (uint32_t)(acc * kOzQ * kOzN);
+        // the pass's nq B tiles lie back to back in the stage (64 rows of
+        // 128 bytes each, 8-row groups 1024 bytes apart), which is one
+        // K-major operand of nq * 64 rows: a single MMA of N = nq * 64 writes
+        // every pair's product into its own 64 accumulator columns
+        const uint32_t idesc = idesc_bf16_f32(kOzM, nq * kOzN);
         for (int kt = 0; kt < KT; ++kt, ++it) {
           const int st = it % kOzStages;
           const uint32_t ph = (uint32_t)(it / kOzStages) & 1u;
@@ -267,13 +272,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           tc_fence_after();
           unsigned char* sa = smem + st * kOzStageBytes;
           const uint64_t da = smem_desc_sw128(sa);
-          for (int qi = 0; qi < nq; ++qi) {
-            const uint64_t db = smem_desc_sw128(sa + kOzABytes + qi * kOzBBytes);
+          const uint64_t db = smem_desc_sw128(sa + kOzABytes);
 #pragma unroll
-            for (int kk = 0; kk < kOzK / 16; ++kk)
-              mma_bf16(dset + (uint32_t)(qi * kOzN), da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
-                       (kt | kk) != 0);
-          }
+          for (int kk = 0; kk < kOzK / 16; ++kk)
+            mma_bf16(dset, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, (kt | kk) != 0);
           mma_commit(&empty[st]);
         }
         mma_commit(&accf[acc]);
