@@ -322,7 +322,7 @@ TaskLayout task_layout(const TaskRef& r, int k, bool split) {
     const size_t pairs = (nw + 31) / 32 + 1;
     sz[10] = pairs * 32 * 32 * sizeof(float2);
     sz[11] = pairs * sizeof(int);
-    sz[12] = ((nw + 7) / 8 + 2) * sizeof(int);  // per-block round counters (block width 8 or 16)
+    sz[12] = 2 * ((nw + 7) / 8 + 2) * sizeof(int);  // per-block round counters of A and V (block width 8 or 16)
   }
   TaskLayout L;
   size_t o = 0;

@@ -49,7 +49,7 @@ struct GateTask {
   double2* V2;          // Nw x Nw scratch: X^3, then the column scales of A W
   float2* Wp;           // fp32 sweeps: each block pair's 32 x 32 rotation W (for the tensor-core rotation)
   int* Wneed;           //   and whether that pair rotated in this round
-  int* qver;            // scheduled fp32 sweeps: rounds finished on each block (nb + 1 entries)
+  int* qver;            // scheduled fp32 sweeps: rounds finished on each block of A, then of V (2 (nb + 1) entries)
 };
 
 // Per-task state written and read by kernels only.

@@ -133,11 +133,69 @@ struct JacobiSmem {
   float2 W[C2][C2];                 // accumulated rotation (16-byte rows)
   unsigned char prs[C2 - 1][NP][2];  // inner circle-method pairs
   int cols[C2];
-  int need, nrot;
+  int need;  // 0: the pair is left alone; 1: it rotates (2 after the V wait of a scheduled launch, 3 if it ran out)
+  int nrot;
   unsigned int smax;
 };
 
 }  // namespace
+
+// ---- Ordering between the CTAs of the scheduled launch (see below)
+
+constexpr unsigned long long kSchedWaitNs = 2000000000ull;
+// q_sweep of a task that no longer sweeps: above every sweep number, so that
+// a wait on any later sweep of that task ends at once (the item is then skipped)
+constexpr int kSweepStopped = 1 << 30;
+
+namespace {
+
+__device__ __forceinline__ unsigned long long sched_clock_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int add_acq_rel_gpu(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// Thread 0 of a CTA: waits until *p >= v. false: the error word is set (this
+// wait ran out, or another CTA's did).
+__device__ bool wait_at_least(const int* p, int v, int* err) {
+  if (ld_acquire_gpu(p) >= v) return true;
+  const unsigned long long t0 = sched_clock_ns();
+  for (;;) {
+    __nanosleep(256);
+    if (ld_acquire_gpu(p) >= v) return true;
+    if (*(volatile int*)err) return false;
+    if (sched_clock_ns() - t0 > kSchedWaitNs) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+}
+
+}  // namespace
+
+// The scheduled launch releases a pair's A columns as soon as they are
+// rotated and rotates its V columns once the previous round has finished
+// with them: aver / vver are the task's per-block counters of rounds done on
+// A and on V, step the item's round number (sweeps included).
+struct PairRelease {
+  int* aver;
+  int* vver;
+  int step;
+  int* err;
+};
 
 // Columns of A32 and V32 are read at L2 (ld.global.cg): under the scheduled
 // launch below, other CTAs of the same launch wrote them.
@@ -151,7 +209,8 @@ __device__ __forceinline__ float2 ld_col(const float2* p) { return __ldcg(p); }
 // only on BW, so a CTA that runs several pairs fills it once).
 template <int BW, bool FUSED>
 __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, int task, int round, int pair,
-                                         unsigned long long* flops, unsigned char* jsm_raw, bool make_prs) {
+                                         unsigned long long* flops, unsigned char* jsm_raw, bool make_prs,
+                                         const PairRelease* rel = nullptr) {
   constexpr int C2 = 2 * BW;                // columns of a block pair
   constexpr int NP = C2 / 2;                // disjoint rotations per inner round
   constexpr int RCH = kRch;
@@ -423,7 +482,8 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
     float2* const M = isA ? A : Vm;
     const int rows = isA ? Mw : Nw;
     const int r0 = (isA ? ch : ch - nch_a) * RCH;
-    if (ch + 1 < nch) {
+    const bool at_v = rel && ch + 1 == nch_a;  // V is fetched only after its wait below
+    if (ch + 1 < nch && !at_v) {
       const bool nA = ch + 1 < nch_a;
       fetch(nA ? A : Vm, nA ? Mw : Nw, (nA ? ch + 1 : ch + 1 - nch_a) * RCH);
     }
@@ -456,8 +516,25 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
         }
       }
     }
-    if (ch + 1 < nch) stash((ch + 1) & 1);
+    if (ch + 1 < nch && !at_v) stash((ch + 1) & 1);
     __syncthreads();
+    if (at_v) {
+      // A_I, A_J are final: the next round may read them. V_I, V_J: wait
+      // until every earlier round has finished with them.
+      if (tid == 0) {
+        __threadfence();
+        st_release_gpu(rel->aver + I, rel->step + 1);
+        st_release_gpu(rel->aver + J, rel->step + 1);
+        need = wait_at_least(rel->vver + I, rel->step, rel->err) && wait_at_least(rel->vver + J, rel->step, rel->err)
+                   ? 2
+                   : 3;
+      }
+      __syncthreads();
+      if (need == 3) return;  // a wait ran out: the launch is abandoned
+      fetch(Vm, Nw, 0);
+      stash((ch + 1) & 1);
+      __syncthreads();
+    }
   }
   if (tid == 0) {
     mt.rotated = 1;
@@ -481,9 +558,12 @@ __global__ void __launch_bounds__(256, 3)
 // then by round, task and pair. A CTA takes the next number from a counter,
 // waits until the item's inputs are final, runs the pair (steps 1-4) and
 // reports it. An item depends on the two items of the previous round of its
-// own task that last wrote its blocks I and J (per-block round counters,
-// qver) and, in the first round of a sweep, on the decision taken at the end
-// of the task's previous sweep. The
+// own task that last wrote its blocks I and J, and, in the first round of a
+// sweep, on the decision taken at the end of the task's previous sweep. The
+// dependency on A and on V is tracked apart (per-block round counters of
+// each, qver): a pair releases A_I, A_J as soon as it has rotated them, so
+// the next round's Gram can start while it rotates V_I, V_J, which it does
+// once the previous round has finished with them. The
 // numbering is a topological order of these dependencies and a CTA takes an
 // item only while it runs, so the unfinished item with the smallest number
 // always has its inputs ready and every wait ends. Each wait is bounded all
@@ -507,58 +587,14 @@ struct F32Sched {
 };
 static_assert(sizeof(F32Sched) <= 16, "fits the handle's counter words 4..7");
 
-constexpr unsigned long long kSchedWaitNs = 2000000000ull;
-// q_sweep of a task that no longer sweeps: above every sweep number, so that
-// a wait on any later sweep of that task ends at once (the item is then skipped)
-constexpr int kSweepStopped = 1 << 30;
-
-namespace {
-
-__device__ __forceinline__ unsigned long long sched_clock_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_gpu(int* p, int v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ int add_acq_rel_gpu(int* p, int v) {
-  int old;
-  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
-
-// Thread 0 of a CTA: waits until *p >= v. false: the error word is set (this
-// wait ran out, or another CTA's did).
-__device__ bool wait_at_least(const int* p, int v, int* err) {
-  if (ld_acquire_gpu(p) >= v) return true;
-  const unsigned long long t0 = sched_clock_ns();
-  for (;;) {
-    __nanosleep(256);
-    if (ld_acquire_gpu(p) >= v) return true;
-    if (*(volatile int*)err) return false;
-    if (sched_clock_ns() - t0 > kSchedWaitNs) {
-      atomicExch(err, 1);
-      return false;
-    }
-  }
-}
-
-}  // namespace
-
 // One CTA per task: resets its counters and counts it if it sweeps (the
 // launcher zeroes the F32Sched words first).
 template <int BW>
 __global__ void k_f32_sched_setup(const GateTask* tasks, TaskMeta* meta, F32Sched* q) {
   TaskMeta& mt = meta[blockIdx.x];
   const int nb = (mt.Nw + BW - 1) / BW, nbe = nb + (nb & 1);
-  int* ver = tasks[blockIdx.x].qver;
-  for (int b = threadIdx.x; b < nbe; b += blockDim.x) ver[b] = 0;
+  int* ver = tasks[blockIdx.x].qver;  // [0, nbe): rounds done on A; [nbe, 2 nbe): on V
+  for (int b = threadIdx.x; b < 2 * nbe; b += blockDim.x) ver[b] = 0;
   if (threadIdx.x == 0) {
     mt.q_done = 0;
     if (mt.active && mt.Nw < 1) {  // no pair: one empty sweep, as the per-round launches
@@ -589,13 +625,16 @@ __global__ void __launch_bounds__(256, 3)
       S.prs[e / NP][e % NP][1] = (unsigned char)qq;
     }
   }
+  constexpr unsigned long long kNone = ~0ull;
+  unsigned long long w_next = kNone;  // thread 0: the next item's number, taken ahead
   for (;;) {
     if (threadIdx.x == 0) {
       int t = -1, r = 0, p = 0, s = 0;
       for (;;) {
         t = -1;
         if (*(volatile int*)&q->n_active == 0 || *(volatile int*)err) break;
-        const unsigned long long w = atomicAdd(&q->head, 1ull);
+        const unsigned long long w = w_next != kNone ? w_next : atomicAdd(&q->head, 1ull);
+        w_next = kNone;
         if (w >= total) break;
         unsigned long long x = w;
         p = (int)(x % (unsigned)p_ub);
@@ -623,22 +662,41 @@ __global__ void __launch_bounds__(256, 3)
       item[1] = r;
       item[2] = p;
       item[3] = s;
+      // take the next number now: the counter's latency hides behind this
+      // item, and the next item's inputs get this item's duration to become
+      // final. Items are still run in the order taken, so the argument above
+      // holds: a CTA that holds an unfinished item is running an earlier one
+      // or waiting on inputs of smaller number.
+      if (t >= 0) w_next = atomicAdd(&q->head, 1ull);
     }
     __syncthreads();
     const int t = item[0], r = item[1], p = item[2], s = item[3];
     if (t < 0) return;
-    pair_f32<BW, true>(tasks, meta, t, r, p, flops, jsm_raw, false);
+    int step = 0, nbe_t = 0;
+    {
+      const TaskMeta& mt = meta[t];
+      const int nb = (mt.Nw + BW - 1) / BW;
+      nbe_t = nb + (nb & 1);
+      step = s * (nbe_t - 1) + r;
+    }
+    const PairRelease rel = {tasks[t].qver, tasks[t].qver + nbe_t, step, err};
+    pair_f32<BW, true>(tasks, meta, t, r, p, flops, jsm_raw, false, &rel);
     __syncthreads();
     if (threadIdx.x == 0) {
       TaskMeta& mt = meta[t];
-      const int nb = (mt.Nw + BW - 1) / BW, nbe = nb + (nb & 1);
-      const int nr = nbe - 1, per_sweep = nr * (nbe / 2);
+      const int nr = nbe_t - 1, per_sweep = nr * (nbe_t / 2);
       int I, J;
-      rr_pair_f(nbe, r, p, I, J);
-      int* ver = tasks[t].qver;
+      rr_pair_f(nbe_t, r, p, I, J);
+      const int need = reinterpret_cast<const JacobiSmem<BW>*>(jsm_raw)->need;
       __threadfence();
-      st_release_gpu(ver + I, s * nr + r + 1);
-      st_release_gpu(ver + J, s * nr + r + 1);
+      if (need == 0) {  // no rotation: A is released here (a rotating pair released it after rotating A)
+        st_release_gpu(rel.aver + I, step + 1);
+        st_release_gpu(rel.aver + J, step + 1);
+      }
+      // V: one more round done on blocks I and J. Counted, not stored: a pair
+      // of the next round that does not rotate may count before this one has.
+      atomicAdd(rel.vver + I, 1);
+      atomicAdd(rel.vver + J, 1);
       if (add_acq_rel_gpu(&mt.q_done, 1) + 1 == (s + 1) * per_sweep) {
         // end of the task's sweep s (the end-of-sweep rule without a failure at the limit)
         mt.sweeps += 1;
