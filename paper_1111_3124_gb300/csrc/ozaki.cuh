@@ -20,12 +20,21 @@ struct OzView {
 
 // One GEMM C = alpha * A B (A: M x K view a, B: K x N given as the N x K view
 // b); C is complex binary64, column-major: C[r + n * ldc].
+// herm = 1 declares row r of A to be conj(column r of B) up to one common
+// sign (A^H A, V^H V, X X with X skew-Hermitian, Q Q with Q Hermitian; M = N):
+// every slice of row r of A is then the conjugate of the same slice of column
+// r of B with the same scale, the set of slice pairs is symmetric and every
+// sum is an exact integer, so the computed C is exactly Hermitian. Only the
+// tiles on and above the diagonal are multiplied; each one above writes its
+// conjugate transpose below as well, which is the value that tile would have
+// produced, bit for bit.
 struct OzJob {
   OzView a, b;
   int M, N, K;
   double2* C;
   long long ldc;
   double alpha;
+  int herm;
 };
 
 // Device scratch for slices and scales, grown on demand by ozaki_zgemm.

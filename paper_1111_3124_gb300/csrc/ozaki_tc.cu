@@ -209,6 +209,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   const int n0 = blockIdx.x * kOzN;
   const int Kc = min(jb.K - k0, kchunk);  // this chunk of the inner dimension
   if (m0 >= 2 * jb.M || n0 >= jb.N || Kc <= 0) return;  // uniform across the CTA
+  // Hermitian product: the 64 x 64 complex tiles below the diagonal are
+  // written by their mirror tiles (128 rows of A^ are 64 complex rows)
+  if (jb.herm && blockIdx.y > blockIdx.x) return;
+  const bool mirror = jb.herm && blockIdx.y < blockIdx.x;
   const int KT = (2 * Kc + kOzK - 1) / kOzK;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -338,6 +342,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             const double val = ldexp((double)hi[j], e - 7 * dh) + ldexp((double)lo[j], e - 7 * (s + 1));
             double* c = &C[2 * ((size_t)r + (size_t)n * jb.ldc) + part];
             *c = k0 > 0 ? *c + jb.alpha * val : jb.alpha * val;  // later K chunks accumulate
+            if (mirror) {  // C[n][r] = conj(C[r][n])
+              const double mv = part ? -val : val;
+              double* cm = &C[2 * ((size_t)n + (size_t)r * jb.ldc) + part];
+              *cm = k0 > 0 ? *cm + jb.alpha * mv : jb.alpha * mv;
+            }
           }
         }
       }

@@ -63,6 +63,7 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
       j.K = mt.Mw;
       j.C = tk.P;
       j.ldc = nw;
+      j.herm = 1;
       break;
     case kOzXX:  // Q = P P
     case kOzX3:  // V2 = P Q
@@ -75,6 +76,7 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
       j.M = j.N = j.K = nw;
       j.C = kind == kOzXX ? tk.Q : tk.V2;
       j.ldc = nw;
+      j.herm = kind == kOzXX;  // X X, X skew-Hermitian (X^3 = X Q is skew only up to rounding: X Q != Q X)
       break;
     case kOzX4:  // T = Q Q
       j.a.p = tk.Q;
@@ -86,6 +88,7 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
       j.M = j.N = j.K = nw;
       j.C = tk.T;
       j.ldc = nw;
+      j.herm = 1;
       break;
     case kOzAW:  // T = (A D^-1)(D P), D = diag(||a_k||) (k_gram_scales): each
                  // column of the product keeps its rounding relative to its own norm
@@ -144,6 +147,7 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
       j.M = j.N = j.K = mt.Nw;
       j.C = tk.P;
       j.ldc = mt.Nw;
+      j.herm = 1;
       break;
     case kOzVP:  // Q = V P
       j.a.p = tk.V;
@@ -171,9 +175,15 @@ __global__ void k_oz_jobs(const GateTask* tasks, const TaskMeta* meta, OzJob* jo
       break;
   }
   jobs[t] = j;
-  if (flops)  // tensor-core flops of the s(s+1)/2 slice pairs of this job (8 per complex multiply-add)
-    atomicAdd(flops, (unsigned long long)(s * (s + 1) / 2) * 8ull * (unsigned long long)j.M *
-                         (unsigned long long)j.N * (unsigned long long)j.K);
+  if (flops) {  // tensor-core flops of the s(s+1)/2 slice pairs of this job (8 per complex multiply-add)
+    unsigned long long f = (unsigned long long)(s * (s + 1) / 2) * 8ull * (unsigned long long)j.M *
+                           (unsigned long long)j.N * (unsigned long long)j.K;
+    if (j.herm) {  // the tiles on and above the diagonal only
+      const unsigned long long nt = (unsigned long long)(j.N + 63) / 64;
+      f = f / (nt * nt) * (nt * (nt + 1) / 2);
+    }
+    atomicAdd(flops, f);
+  }
 }
 
 // theta[(i,a),(j,b)] = sum_{kl} U[(ij),(kl)] T[(k,a),(l,b)], written as the

@@ -69,6 +69,24 @@ def test_split_gemm_long_k_in_chunks(torch, k):
     assert _gemm_err(torch, 130, 70, k, seed=k) < 8e-15
 
 
+@pytest.mark.parametrize("m,k", [(200, 130), (512, 700), (1024, 1300)])
+def test_split_gram_is_exactly_hermitian(torch, m, k):
+    # A^H A from conj(A)^T and A: every digit product is an exact integer and
+    # the slice pairs are symmetric, so the product is Hermitian bit for bit.
+    # The update's Gram and Newton-Schulz products rely on this: they multiply
+    # the tiles on and above the diagonal and mirror them.
+    from paper_1111_3124_gb300.mps import split_zgemm
+    rng = np.random.default_rng(m + k)
+    A = rng.standard_normal((k, m)) + 1j * rng.standard_normal((k, m))
+    A *= (2.0 ** rng.integers(-20, 20, size=m))[None, :]
+    Ah = np.ascontiguousarray(A.conj().T)
+    C = split_zgemm(torch.from_numpy(Ah).cuda(), torch.from_numpy(A).cuda(), 8).cpu().numpy()
+    assert np.array_equal(C, C.conj().T)
+    assert np.all(np.diag(C).imag == 0)
+    bound = np.abs(Ah) @ np.abs(A)
+    assert np.max(np.abs(C - Ah @ A) / bound) < 8e-15
+
+
 # ------------------------------------------------------------- split updates ---
 
 def split_mps(n, chi_max, cutoff):
