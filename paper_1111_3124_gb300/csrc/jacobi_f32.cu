@@ -13,11 +13,12 @@
 //      zero columns excluded at binary64 resolution); a pair that passes is
 //      left alone.
 //   3. One cyclic sweep of the two-sided Hermitian Jacobi method on G
-//      (circle-method rounds of 2b/2 disjoint rotations). A round is two
-//      barriers: in every warp, lane l forms the rotation of pair l and the
+//      (circle-method rounds of 2b/2 disjoint rotations). A round is one
+//      barrier: in every warp, lane l forms the rotation of pair l and the
 //      threads take those of their row pair and column pair by shuffle, read
 //      the 2 x 2 block of G those rotations touch, then write J_i^H G_blk J_j
-//      back; the product W of the rotations is accumulated in the same pass.
+//      into the other of two copies of G (every block is written, changed or
+//      not); the product W of the rotations is accumulated in the same pass.
 //      The rotation of a 2 x 2 Hermitian problem [a g; conj(g) b] is the real
 //      symmetric Schur rotation (Golub & Van Loan) conjugated by
 //      diag(e^{i phi}, 1): t e^{i phi} = 2 sign(d) g / (|d| + sqrt(d^2 + 4|g|^2)),
@@ -129,8 +130,8 @@ template <int BW>
 struct JacobiSmem {
   static constexpr int C2 = 2 * BW, NP = BW, LD = C2 + 1;
   float2 buf[2][kRch][LD];          // staged chunks; the Gram's partial tiles
-  float2 G[C2][LD];                 // Gram of the block pair
-  float2 W[C2][C2];                 // accumulated rotation (16-byte rows)
+  float2 G[2][C2][LD];              // Gram of the block pair; the inner sweep alternates the two copies
+  float2 W[C2][C2 + 2];             // accumulated rotation (16-byte aligned rows, padded against bank conflicts)
   unsigned char prs[C2 - 1][NP][2];  // inner circle-method pairs
   int cols[C2];
   int need;  // 0: the pair is left alone; 1: it rotates (2 after the V wait of a scheduled launch, 3 if it ran out)
@@ -244,7 +245,7 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
   JacobiSmem<BW>& S = *reinterpret_cast<JacobiSmem<BW>*>(jsm_raw);
   int* const cols = S.cols;
   auto& buf = S.buf;
-  auto& G = S.G;
+  auto& G = S.G[0];  // the Gram and the test; the inner sweep reads S.G[it & 1] and writes the other
   auto& W = S.W;
   auto& prs = S.prs;
   int& need = S.need;
@@ -325,17 +326,19 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
     if (ch + 1 < nch_a) stash((ch + 1) & 1);
     __syncthreads();
   }
-  // partial tiles -> G (fixed summation order over the parts)
+  // partial tiles -> G (fixed summation order over the parts); entry-major,
+  // so that a warp's stores and a warp's loads touch consecutive words
+  constexpr int NSLOT = NT * NPART;
   float2* red = &buf[0][0][0];
   if (gtile < NT) {
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) red[(gtile * NPART + gpart) * 16 + a * 4 + b] = acc[a][b];
+      for (int b = 0; b < 4; ++b) red[(a * 4 + b) * NSLOT + gtile * NPART + gpart] = acc[a][b];
   }
   __syncthreads();
   for (int e = tid; e < NT * 16; e += 256) {
-    const int tile = e / 16, ent = e % 16;
+    const int tile = e % NT, ent = e / NT;
     int ri = 0, rem = tile;
     while (rem >= TB - ri) {
       rem -= TB - ri;
@@ -343,7 +346,7 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
     }
     const int rj = ri + rem;
     float2 s = zero;
-    for (int part = 0; part < NPART; ++part) s = f_add(s, red[(tile * NPART + part) * 16 + ent]);
+    for (int part = 0; part < NPART; ++part) s = f_add(s, red[ent * NSLOT + tile * NPART + part]);
     const int p = 4 * ri + ent / 4, q = 4 * rj + ent % 4;
     if (p < q) {
       G[p][q] = s;
@@ -394,6 +397,8 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
   const bool blk_warp = (tid & ~31) < NP * NP;  // warps holding 2 x 2 blocks (NP * NP is a multiple of 32)
   for (int it = 0; it < kF32InnerSweeps * (C2 - 1); ++it) {
     const int ir = it % (C2 - 1);
+    auto& Gc = S.G[it & 1];        // this round reads one copy of G ...
+    auto& Gn = S.G[(it & 1) ^ 1];  // ... and writes all of the other: one barrier per round
     Rot ri = {1.f, zero, 0.f, false}, rj = ri;
     int Pi = 0, Qi = 0, Pj = 0, Qj = 0;
     float2 x00 = zero, x01 = zero, x10 = zero, x11 = zero;
@@ -404,7 +409,7 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
       Rot mine = {1.f, zero, 0.f, false};
       if (lane < NP) {
         const int Pl = prs[ir][lane][0], Ql = prs[ir][lane][1];
-        mine = make_rot(G[Pl][Pl].x, G[Ql][Ql].x, G[Pl][Ql], tinyf);
+        mine = make_rot(Gc[Pl][Pl].x, Gc[Ql][Ql].x, Gc[Pl][Ql], tinyf);
       }
       ri = shfl_rot(mine, bi % 32);
       rj = shfl_rot(mine, bj);
@@ -413,10 +418,10 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
       Pj = prs[ir][bj][0];
       Qj = prs[ir][bj][1];
       if (tid < NP * NP) {
-        x00 = G[Pi][Pj];
-        x01 = G[Pi][Qj];
-        x10 = G[Qi][Pj];
-        x11 = G[Qi][Qj];
+        x00 = Gc[Pi][Pj];
+        x01 = Gc[Pi][Qj];
+        x10 = Gc[Qi][Pj];
+        x11 = Gc[Qi][Qj];
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
           w[m][0] = W[bi + NP * m][Pj];
@@ -424,15 +429,19 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
         }
       }
     }
-    __syncthreads();
     if (tid < NP * NP) {
       if (bi == bj) {
         if (ri.on) {
-          G[Pi][Pi] = make_float2(x00.x - ri.tg, 0.f);
-          G[Qi][Qi] = make_float2(x11.x + ri.tg, 0.f);
-          G[Pi][Qi] = zero;
-          G[Qi][Pi] = zero;
+          Gn[Pi][Pi] = make_float2(x00.x - ri.tg, 0.f);
+          Gn[Qi][Qi] = make_float2(x11.x + ri.tg, 0.f);
+          Gn[Pi][Qi] = zero;
+          Gn[Qi][Pi] = zero;
           atomicAdd(&nrot, 1);
+        } else {
+          Gn[Pi][Pi] = x00;
+          Gn[Pi][Qi] = x01;
+          Gn[Qi][Pi] = x10;
+          Gn[Qi][Qi] = x11;
         }
       } else if (ri.on || rj.on) {
         // rows: Y = J_i^H X (row P' = c X_P - se X_Q, row Q' = conj(se) X_P + c X_Q)
@@ -441,10 +450,15 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
         const float2 y10 = f_add(f_mul(f_conj(ri.se), x00), f_scale(ri.c, x10));
         const float2 y11 = f_add(f_mul(f_conj(ri.se), x01), f_scale(ri.c, x11));
         // columns: Z = Y J_j (col P' = c Y_P - conj(se) Y_Q, col Q' = se Y_P + c Y_Q)
-        G[Pi][Pj] = f_sub(f_scale(rj.c, y00), f_mul(f_conj(rj.se), y01));
-        G[Qi][Pj] = f_sub(f_scale(rj.c, y10), f_mul(f_conj(rj.se), y11));
-        G[Pi][Qj] = f_add(f_mul(rj.se, y00), f_scale(rj.c, y01));
-        G[Qi][Qj] = f_add(f_mul(rj.se, y10), f_scale(rj.c, y11));
+        Gn[Pi][Pj] = f_sub(f_scale(rj.c, y00), f_mul(f_conj(rj.se), y01));
+        Gn[Qi][Pj] = f_sub(f_scale(rj.c, y10), f_mul(f_conj(rj.se), y11));
+        Gn[Pi][Qj] = f_add(f_mul(rj.se, y00), f_scale(rj.c, y01));
+        Gn[Qi][Qj] = f_add(f_mul(rj.se, y10), f_scale(rj.c, y11));
+      } else {
+        Gn[Pi][Pj] = x00;
+        Gn[Pi][Qj] = x01;
+        Gn[Qi][Pj] = x10;
+        Gn[Qi][Qj] = x11;
       }
       if (rj.on) {
 #pragma unroll
