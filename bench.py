@@ -820,7 +820,7 @@ def run_gpu(a):
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MiB buffer written between timed steps; working set > L2",
                        "tuning": {"table (nw_max, fp32 block, launch mode: 0 per round, 1 tensor-core rotation, "
-                                  "2 scheduled)": tune_table,
+                                  "2 scheduled, 3 scheduled 384-thread CTAs)": tune_table,
                                   "source": tune_source},
                        "max_bond": int(max(chi)) if len(chi) else 1},
             "roofline": roof, "kernels": kernels, "clocks": clocks,
@@ -871,7 +871,8 @@ F32_CAPTURED = {0: (146.0e6, 0.1697), 2: (42.16e9, 60.91)}
 
 def f32_mode(tune_table, nw):
     """(block width, launch mode) the tuning table gives the fp32 sweeps at
-    width nw (the library's default without a table: 16, scheduled)."""
+    width nw (the library's default without a table: 16, scheduled with
+    256-thread CTAs)."""
     bw, mode = 16, 2
     for nw_max, b, md in (tune_table or []):
         bw, mode = b, md
@@ -882,8 +883,9 @@ def f32_mode(tune_table, nw):
 
 def f32_kernel_name(tune_table, nw):
     bw, mode = f32_mode(tune_table, nw)
-    if mode == 2:
-        return "k_jacobi_f32_sched<%d> (fp32 preconditioning sweeps, one scheduled launch per pass)" % bw
+    if mode in (2, 3):
+        return "k_jacobi_f32_sched<%d, %d> (fp32 preconditioning sweeps, one scheduled launch per pass)" % (
+            bw, 256 if mode == 2 else 384)
     if mode == 1:
         return "k_jacobi_pair_f32<16> + k_rot_tc (fp32 preconditioning sweeps, tensor-core rotation)"
     return "k_jacobi_pair_f32<%d> (fp32 preconditioning sweeps, one launch per round)" % bw

@@ -139,9 +139,11 @@ int mps_set_limits(mps_handle h, int max_sweeps);
  * one round of block pairs at a time with the rotation in the pair kernel,
  * 1 does the same with the block rotations on the tensor cores (block width
  * 16 only), 2 runs every sweep of every task of the pass in one scheduled
- * launch (pairs taken in order as their inputs become final). All three
- * compute the same rotations; 0 and 2 give identical results. n = 0 restores
- * the default (16, mode 2). Host arrays. Errors: MPS_ERR_ARG. */
+ * launch (pairs taken in order as their inputs become final) of 256-thread
+ * CTAs, 3 the same with 384-thread CTAs (fewer, faster pairs at a time). All
+ * four compute the same rotations; 0 and 2 give identical results (3 sums
+ * each Gram over a different grouping of rows). n = 0 restores the default
+ * (16, mode 2). Host arrays. Errors: MPS_ERR_ARG. */
 int mps_set_tuning(mps_handle h, int n, const int* nw_max, const int* f32_block, const int* f32_mode);
 
 /* mps_debug_fail_alloc - test hook for the allocation-failure path (no paper

@@ -53,8 +53,8 @@ constexpr int kF32Sweeps = 30;
 constexpr int kGramSteps = 3;  // simultaneous-rotation steps of the split path's Gram polish
 // How the fp32 sweeps are launched (mps_set_tuning): one launch per round with
 // the rotation in the pair kernel, or on the tensor cores; or every sweep in
-// one scheduled launch (the default).
-constexpr int kF32ModePair = 0, kF32ModeTc = 1, kF32ModeSched = 2;
+// one scheduled launch of 256-thread CTAs (the default), or of 384-thread CTAs.
+constexpr int kF32ModePair = 0, kF32ModeTc = 1, kF32ModeSched = 2, kF32ModeSchedWide = 3;
 
 // Memory budget of one batched pass: the tasks of a layer (or of many
 // circuits' layers) are processed in chunks whose workspace fits this.
@@ -102,7 +102,7 @@ struct mps_state {
   int prec = MPS_PREC_FP64, slices = 8, svd_mode = 0;
   int max_sweeps = kMaxSweeps;  // binary64 Jacobi sweep limit (mps_set_limits)
   // per working-matrix width: fp32 block width and launch mode (mps_set_tuning);
-  // empty: block width 16, all sweeps in one scheduled launch
+  // empty: block width 16, all sweeps in one scheduled launch of 256-thread CTAs
   struct Tune {
     int nw_max, f32_block, mode;  // mode: how the fp32 sweeps are launched (kF32Mode*)
   };
@@ -624,9 +624,10 @@ int run_f32_sweeps(mps_state* h, int ng, int mw_ub, int nw_ub) {
     mode = t.mode;
     if (nw_ub <= t.nw_max) break;
   }
-  if (mode == kF32ModeSched) {
+  if (mode == kF32ModeSched || mode == kF32ModeSchedWide) {
     const int ev = pbeg(h);
-    const int nl = launch_jacobi_f32_sched(h->d_tasks, h->d_meta, ng, nw_ub, bw, kF32Sweeps, h->d_counter + 4,
+    const int nl = launch_jacobi_f32_sched(h->d_tasks, h->d_meta, ng, nw_ub, bw, mode == kF32ModeSched ? 256 : 384,
+                                           kF32Sweeps, h->d_counter + 4,
                                            h->d_oz_err, fl, h->stream);
     if (nl < 0) {
       const cudaError_t e = cudaGetLastError();
@@ -2146,7 +2147,8 @@ int mps_set_tuning(mps_handle h, int n, const int* nw_max, const int* f32_block,
   std::vector<mps_state::Tune> t(n);
   for (int i = 0; i < n; ++i) {
     if (f32_block[i] != 8 && f32_block[i] != 16) return fail(MPS_ERR_ARG, "fp32 block width must be 8 or 16");
-    if (f32_mode[i] < kF32ModePair || f32_mode[i] > kF32ModeSched) return fail(MPS_ERR_ARG, "fp32 mode must be 0, 1 or 2");
+    if (f32_mode[i] < kF32ModePair || f32_mode[i] > kF32ModeSchedWide)
+      return fail(MPS_ERR_ARG, "fp32 mode must be 0, 1, 2 or 3");
     if (f32_mode[i] == kF32ModeTc && f32_block[i] != 16)
       return fail(MPS_ERR_ARG, "the tensor-core rotation needs block width 16");
     if (i > 0 && nw_max[i] <= nw_max[i - 1]) return fail(MPS_ERR_ARG, "widths must increase");

@@ -126,10 +126,10 @@ __device__ __forceinline__ Rot shfl_rot(const Rot& r, int src) {
 constexpr int kRch = 64;  // rows per staged chunk
 
 // Shared memory of one CTA (dynamic: above the 48 KB static limit).
-template <int BW>
+template <int BW, int RCH = kRch>
 struct JacobiSmem {
   static constexpr int C2 = 2 * BW, NP = BW, LD = C2 + 1;
-  float2 buf[2][kRch][LD];          // staged chunks; the Gram's partial tiles
+  float2 buf[2][RCH][LD];           // staged chunks; the Gram's partial tiles
   float2 G[2][C2][LD];              // Gram of the block pair; the inner sweep alternates the two copies
   float2 W[C2][C2 + 2];             // accumulated rotation (16-byte aligned rows, padded against bank conflicts)
   unsigned char prs[C2 - 1][NP][2];  // inner circle-method pairs
@@ -208,24 +208,24 @@ __device__ __forceinline__ float2 ld_col(const float2* p) { return __ldcg(p); }
 // Wneed, and k_rot_tc applies W on the tensor cores. Every early return is
 // taken by the whole CTA. make_prs: fill the inner pairing table (it depends
 // only on BW, so a CTA that runs several pairs fills it once).
-template <int BW, bool FUSED>
+template <int BW, bool FUSED, int NTHR = 256>
 __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, int task, int round, int pair,
                                          unsigned long long* flops, unsigned char* jsm_raw, bool make_prs,
                                          const PairRelease* rel = nullptr) {
   constexpr int C2 = 2 * BW;                // columns of a block pair
   constexpr int NP = C2 / 2;                // disjoint rotations per inner round
-  constexpr int RCH = kRch;
+  constexpr int RCH = NTHR / 4;             // rows per staged chunk (kRch at 256 threads)
   constexpr int LD = C2 + 1;                // padded chunk row, in float2
-  constexpr int PER = RCH * C2 / 256;       // staged elements per thread
+  constexpr int PER = RCH * C2 / NTHR;       // staged elements per thread
   constexpr int TB = C2 / 4;                // 4 x 4 Gram tiles per dimension
   constexpr int NT = TB * (TB + 1) / 2;     // upper-triangle tiles
   constexpr int RED = 2 * RCH * LD / 16;    // partial tiles the chunk buffers hold
-  constexpr int NPART0 = 256 / NT;
+  constexpr int NPART0 = NTHR / NT;
   constexpr int NPART = NPART0 * NT <= RED ? NPART0 : RED / NT;  // threads per tile
   constexpr int NCG = C2 / 4;               // rotation: column groups of 4
-  constexpr int SLOTS = 256 / NCG;          // rotation: row slots
+  constexpr int SLOTS = NTHR / NCG;          // rotation: row slots
   constexpr int TR = RCH / SLOTS;           // rotation: rows per thread and chunk
-  static_assert(NP * NP <= 256 && RCH * C2 % 256 == 0 && RCH % SLOTS == 0, "tiling");
+  static_assert(NP * NP <= NTHR && RCH * C2 % NTHR == 0 && RCH % SLOTS == 0, "tiling");
   static_assert(NPART >= 1, "Gram tiling");
   static_assert(NP * NP % 32 == 0 && NP <= 32, "2 x 2 blocks fill whole warps");
 
@@ -242,7 +242,7 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
   float2* const Vm = tk.V32;
   const float2 zero = make_float2(0.f, 0.f);
 
-  JacobiSmem<BW>& S = *reinterpret_cast<JacobiSmem<BW>*>(jsm_raw);
+  JacobiSmem<BW, RCH>& S = *reinterpret_cast<JacobiSmem<BW, RCH>*>(jsm_raw);
   int* const cols = S.cols;
   auto& buf = S.buf;
   auto& G = S.G[0];  // the Gram and the test; the inner sweep reads S.G[it & 1] and writes the other
@@ -257,7 +257,7 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
     const int j = blk * BW + (tid % BW);
     cols[tid] = (blk < nb && j < Nw) ? j : -1;
   }
-  for (int e = tid; make_prs && e < (C2 - 1) * NP; e += 256) {
+  for (int e = tid; make_prs && e < (C2 - 1) * NP; e += NTHR) {
     int p, q;
     rr_pair_f(C2, e / NP, e % NP, p, q);
     prs[e / NP][e % NP][0] = (unsigned char)p;
@@ -275,7 +275,7 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
   auto fetch = [&](const float2* M, int rows, int r0) {
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
-      const int e = tid + 256 * j, col = e / RCH, row = e % RCH;
+      const int e = tid + NTHR * j, col = e / RCH, row = e % RCH;
       const int gc = cols[col];
       pf[j] = (gc >= 0 && r0 + row < rows) ? ld_col(&M[(size_t)(r0 + row) + (size_t)gc * rows]) : zero;
     }
@@ -283,7 +283,7 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
   auto stash = [&](int b) {
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
-      const int e = tid + 256 * j;
+      const int e = tid + NTHR * j;
       buf[b][e % RCH][e / RCH] = pf[j];
     }
   };
@@ -337,7 +337,7 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
       for (int b = 0; b < 4; ++b) red[(a * 4 + b) * NSLOT + gtile * NPART + gpart] = acc[a][b];
   }
   __syncthreads();
-  for (int e = tid; e < NT * 16; e += 256) {
+  for (int e = tid; e < NT * 16; e += NTHR) {
     const int tile = e % NT, ent = e / NT;
     int ri = 0, rem = tile;
     while (rem >= TB - ri) {
@@ -355,7 +355,7 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
       G[p][p] = make_float2(s.x, 0.f);
     }
   }
-  for (int e = tid; e < C2 * C2; e += 256) W[e / C2][e % C2] = make_float2((e / C2) == (e % C2) ? 1.f : 0.f, 0.f);
+  for (int e = tid; e < C2 * C2; e += NTHR) W[e / C2][e % C2] = make_float2((e / C2) == (e % C2) ? 1.f : 0.f, 0.f);
   __syncthreads();
 
   // ---- 2. test (binary64 zero threshold, fp32 resolution)
@@ -364,7 +364,7 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
   {
     float mx = 0.f;
     int nd = 0;
-    for (int e = tid; e < C2 * C2; e += 256) {
+    for (int e = tid; e < C2 * C2; e += NTHR) {
       const int p = e / C2, q = e % C2;
       if (p >= q) continue;
       const float al = G[p][p].x, be = G[q][q].x;
@@ -473,7 +473,7 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
 
   if (!FUSED) {  // hand W to the tensor-core rotation
     float2* Wo = tk.Wp + (size_t)pair * C2 * C2;
-    for (int e = tid; e < C2 * C2; e += 256) Wo[e] = W[e / C2][e % C2];
+    for (int e = tid; e < C2 * C2; e += NTHR) Wo[e] = W[e / C2][e % C2];
     if (tid == 0) {
       tk.Wneed[pair] = 1;
       mt.rotated = 1;
@@ -623,14 +623,18 @@ __global__ void k_f32_sched_setup(const GateTask* tasks, TaskMeta* meta, F32Sche
   }
 }
 
-template <int BW>
-__global__ void __launch_bounds__(256, 3)
+// NTHR threads per CTA: 256 (three CTAs per SM) or 384 (two per SM: the same
+// warps per SM in fewer pairs at a time; measured slower at Nw = 512 and a
+// little faster at Nw = 256, so the tuner chooses).
+template <int BW, int NTHR>
+__global__ void __launch_bounds__(NTHR, NTHR == 256 ? 3 : 2)
     k_jacobi_f32_sched(const GateTask* tasks, TaskMeta* meta, int ntask, int r_ub, int p_ub, int max_sweeps,
                        unsigned long long total, F32Sched* q, int* err, unsigned long long* flops) {
+  using Smem = JacobiSmem<BW, NTHR / 4>;
   extern __shared__ __align__(16) unsigned char jsm_raw[];
   __shared__ int item[4];  // task (-1: nothing left), round, pair, sweep
   {
-    JacobiSmem<BW>& S = *reinterpret_cast<JacobiSmem<BW>*>(jsm_raw);
+    Smem& S = *reinterpret_cast<Smem*>(jsm_raw);
     constexpr int C2 = 2 * BW, NP = BW;
     for (int e = threadIdx.x; e < (C2 - 1) * NP; e += blockDim.x) {
       int p, qq;
@@ -694,14 +698,14 @@ __global__ void __launch_bounds__(256, 3)
       step = s * (nbe_t - 1) + r;
     }
     const PairRelease rel = {tasks[t].qver, tasks[t].qver + nbe_t, step, err};
-    pair_f32<BW, true>(tasks, meta, t, r, p, flops, jsm_raw, false, &rel);
+    pair_f32<BW, true, NTHR>(tasks, meta, t, r, p, flops, jsm_raw, false, &rel);
     __syncthreads();
     if (threadIdx.x == 0) {
       TaskMeta& mt = meta[t];
       const int nr = nbe_t - 1, per_sweep = nr * (nbe_t / 2);
       int I, J;
       rr_pair_f(nbe_t, r, p, I, J);
-      const int need = reinterpret_cast<const JacobiSmem<BW>*>(jsm_raw)->need;
+      const int need = reinterpret_cast<const Smem*>(jsm_raw)->need;
       __threadfence();
       if (need == 0) {  // no rotation: A is released here (a rotating pair released it after rotating A)
         st_release_gpu(rel.aver + I, step + 1);
@@ -734,22 +738,28 @@ static void launch_pair_f32(const GateTask* t, TaskMeta* m, int ntask, int round
   k_jacobi_pair_f32<BW, FUSED><<<dim3(pairs_ub, ntask), 256, bytes, st>>>(t, m, round, flops);
 }
 
-static int g_sched_ctas[2] = {0, 0};  // resident CTAs of the scheduled kernel (block width 8, 16)
+// resident CTAs of the scheduled kernel: [block width 8, 16][256, 384 threads]
+static int g_sched_ctas[2][2] = {{0, 0}, {0, 0}};
+
+template <int BW, int NTHR>
+static void sched_prepare(int sms) {
+  constexpr int bytes = (int)sizeof(JacobiSmem<BW, NTHR / 4>);
+  cudaFuncSetAttribute(k_jacobi_f32_sched<BW, NTHR>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_jacobi_f32_sched<BW, NTHR>, NTHR, bytes);
+  g_sched_ctas[BW == 8 ? 0 : 1][NTHR == 256 ? 0 : 1] = std::max(1, per) * std::max(1, sms);
+}
 
 void jacobi_f32_prepare() {
   static bool done = false;
   if (done) return;
-  cudaFuncSetAttribute(k_jacobi_f32_sched<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(JacobiSmem<8>));
-  cudaFuncSetAttribute(k_jacobi_f32_sched<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(JacobiSmem<16>));
-  int dev = 0, sms = 0, per8 = 0, per16 = 0;
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per8, k_jacobi_f32_sched<8>, 256, sizeof(JacobiSmem<8>));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per16, k_jacobi_f32_sched<16>, 256, sizeof(JacobiSmem<16>));
-  g_sched_ctas[0] = std::max(1, per8) * std::max(1, sms);
-  g_sched_ctas[1] = std::max(1, per16) * std::max(1, sms);
+  sched_prepare<8, 256>(sms);
+  sched_prepare<16, 256>(sms);
+  sched_prepare<8, 384>(sms);
+  sched_prepare<16, 384>(sms);
   cudaFuncSetAttribute(k_jacobi_pair_f32<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sizeof(JacobiSmem<8>));
   cudaFuncSetAttribute(k_jacobi_pair_f32<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -774,7 +784,7 @@ void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int roun
 // after a set-up of the counters (one CTA per task). sched points to four ints of device
 // memory (8-byte aligned) the launch may overwrite; err is the handle's error
 // word. Returns the number of launches (0 or 2), or -1 when the launch failed.
-int launch_jacobi_f32_sched(const GateTask* t, TaskMeta* m, int ntask, int nw_ub, int bw, int max_sweeps,
+int launch_jacobi_f32_sched(const GateTask* t, TaskMeta* m, int ntask, int nw_ub, int bw, int nthr, int max_sweeps,
                             void* sched, int* err, unsigned long long* flops, cudaStream_t st) {
   jacobi_f32_prepare();
   if (ntask < 1 || nw_ub < 1 || max_sweeps < 1) return 0;
@@ -787,23 +797,32 @@ int launch_jacobi_f32_sched(const GateTask* t, TaskMeta* m, int ntask, int nw_ub
     k_f32_sched_setup<8><<<ntask, 128, 0, st>>>(t, m, q);
   else
     k_f32_sched_setup<16><<<ntask, 128, 0, st>>>(t, m, q);
-  const unsigned long long cap = (unsigned long long)g_sched_ctas[bw == 8 ? 0 : 1];
+  const bool wide = nthr == 384;
+  const unsigned long long cap = (unsigned long long)g_sched_ctas[bw == 8 ? 0 : 1][wide ? 1 : 0];
   // a cooperative launch (every CTA resident at once); the pull order above
   // needs only that a CTA holding an item runs, which any launch gives
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)std::min(total, cap));
-  cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = bw == 8 ? sizeof(JacobiSmem<8>) : sizeof(JacobiSmem<16>);
+  cfg.blockDim = dim3(wide ? 384 : 256);
+  cfg.dynamicSmemBytes = bw == 8 ? (wide ? sizeof(JacobiSmem<8, 96>) : sizeof(JacobiSmem<8>))
+                                 : (wide ? sizeof(JacobiSmem<16, 96>) : sizeof(JacobiSmem<16>));
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const cudaError_t e = bw == 8 ? cudaLaunchKernelEx(&cfg, k_jacobi_f32_sched<8>, t, m, ntask, r_ub, p_ub, max_sweeps,
-                                                     total, q, err, flops)
-                                : cudaLaunchKernelEx(&cfg, k_jacobi_f32_sched<16>, t, m, ntask, r_ub, p_ub, max_sweeps,
-                                                     total, q, err, flops);
+  cudaError_t e;
+  if (bw == 8)
+    e = wide ? cudaLaunchKernelEx(&cfg, k_jacobi_f32_sched<8, 384>, t, m, ntask, r_ub, p_ub, max_sweeps, total, q, err,
+                                  flops)
+             : cudaLaunchKernelEx(&cfg, k_jacobi_f32_sched<8, 256>, t, m, ntask, r_ub, p_ub, max_sweeps, total, q, err,
+                                  flops);
+  else
+    e = wide ? cudaLaunchKernelEx(&cfg, k_jacobi_f32_sched<16, 384>, t, m, ntask, r_ub, p_ub, max_sweeps, total, q,
+                                  err, flops)
+             : cudaLaunchKernelEx(&cfg, k_jacobi_f32_sched<16, 256>, t, m, ntask, r_ub, p_ub, max_sweeps, total, q,
+                                  err, flops);
   return e == cudaSuccess ? 2 : -1;
 }
 

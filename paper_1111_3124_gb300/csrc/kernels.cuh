@@ -37,13 +37,14 @@ void launch_sweep_end_nofail(TaskMeta* m, int ntask, int max_sweeps, int* active
 void launch_jacobi_round_f32(const GateTask* t, TaskMeta* m, int ntask, int round, int pairs_ub, int bw, int fused,
                              unsigned long long* flops, cudaStream_t st);
 // Every fp32 preconditioning sweep of every task in one scheduled launch
-// (fused rotation, bw = 8 or 16, at most max_sweeps sweeps per task): the same
+// (fused rotation, bw = 8 or 16, nthr = 256 or 384 threads per CTA, at most
+// max_sweeps sweeps per task): the same
 // pairs, rounds and sweeps as launch_jacobi_round_f32 with the end-of-sweep
 // rule of launch_sweep_end_nofail, taken per task on the device. sched: four
 // ints of device scratch (8-byte aligned); err: the handle's error word (set
 // when a bounded dependency wait runs out). Returns the launches made, or -1
 // when the (cooperative) launch failed.
-int launch_jacobi_f32_sched(const GateTask* t, TaskMeta* m, int ntask, int nw_ub, int bw, int max_sweeps,
+int launch_jacobi_f32_sched(const GateTask* t, TaskMeta* m, int ntask, int nw_ub, int bw, int nthr, int max_sweeps,
                             void* sched, int* err, unsigned long long* flops, cudaStream_t st);
 // One-time kernel attributes (shared-memory sizes), set before a program
 // records launches into a graph; the launchers call them too.

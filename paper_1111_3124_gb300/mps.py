@@ -198,7 +198,8 @@ class MPS:
     def set_tuning(self, table) -> None:
         """table: list of (nw_max, f32_block, mode), nw_max increasing; mode 0
         launches the fp32 sweeps per round, 1 per round with the rotation on
-        the tensor cores, 2 all sweeps in one scheduled launch (the default)."""
+        the tensor cores, 2 all sweeps in one scheduled launch of 256-thread
+        CTAs (the default), 3 the same with 384-thread CTAs."""
         nw = np.ascontiguousarray([t[0] for t in table] or [0], dtype=np.int32)
         bw = np.ascontiguousarray([t[1] for t in table] or [0], dtype=np.int32)
         tc = np.ascontiguousarray([t[2] for t in table] or [0], dtype=np.int32)

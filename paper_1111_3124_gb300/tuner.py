@@ -6,7 +6,7 @@ synthetic state of 64 sites whose bonds sit at chi = Nw / 2 (where the
 chain's ends allow), once per candidate launch
 shape (fp32 block width 8 or 16; one launch per round with the block
 rotations in the pair kernel or on the tensor cores, or every sweep in one
-scheduled launch), and keeps the fastest. The table is cached as JSON and applied
+scheduled launch of 256- or 384-thread CTAs), and keeps the fastest. The table is cached as JSON and applied
 to handles with MPS.set_tuning; nothing here computes any part of the update.
 
   python -m paper_1111_3124_gb300.tuner [--out PATH] [--chis 32 64 128 256]
@@ -21,9 +21,9 @@ import numpy as np
 
 # (fp32 block width, launch mode): 0 one launch per round, rotation in the
 # pair kernel; 1 the same with the rotation on the tensor cores; 2 every sweep
-# in one scheduled launch
-CANDIDATES = [(16, 2), (8, 2), (16, 0), (8, 0), (16, 1)]
-MODE_NAMES = {0: "round", 1: "tc", 2: "sched"}
+# in one scheduled launch of 256-thread CTAs; 3 the same with 384-thread CTAs
+CANDIDATES = [(16, 3), (8, 3), (16, 2), (8, 2), (16, 0), (8, 0), (16, 1)]
+MODE_NAMES = {0: "round", 1: "tc", 2: "sched", 3: "sched384"}
 DEFAULT_CHIS = (32, 64, 128, 256)
 
 

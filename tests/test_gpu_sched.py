@@ -3,7 +3,8 @@ launch, block pairs taken in order as their inputs become final) against one
 launch per round-robin round. Both run the same rotations on the same data, so
 the states must agree bit for bit: eagerly, in recorded programs, for U(8)
 gates and for passes that mix widths and circuits. The oracle checks the
-scheduled result on its own as well."""
+scheduled result on its own as well, and the 384-thread form of the scheduled
+launch, whose Grams sum their rows in another grouping."""
 import numpy as np
 import pytest
 
@@ -13,7 +14,7 @@ from tests.helpers import spectrum_err
 
 pytestmark = pytest.mark.gpu
 
-ROUND, SCHED = 0, 2  # launch modes of mps_set_tuning
+ROUND, SCHED, SCHED384 = 0, 2, 3  # launch modes of mps_set_tuning
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -143,3 +144,30 @@ def test_many_circuits_of_mixed_size_in_shared_passes():
                 m.close()
     for a, b in zip(results[ROUND], results[SCHED]):
         _same(a, b)
+
+
+@pytest.mark.parametrize("bw", [16, 8])
+def test_384_thread_ctas_match_the_oracle(bw):
+    rng = np.random.default_rng(960 + bw)
+    n, chi = 16, 64
+    state = _saturated_state(n, chi, rng)
+    layers = [[(s, C.haar_unitary(4, rng)) for s in C.brickwork_sites(n, p)] for p in (0, 1, 0)]
+    b, _ = _run_eager(n, chi, [(4096, bw, SCHED384)], layers, state)
+    o = oracle.OracleMPS(n, chi, 1e-12)
+    o.set_state(*state)
+    for layer in layers:
+        for s, U in layer:
+            o.apply_gate(s, U)
+    for bnd in range(n - 1):
+        assert spectrum_err(b[2][bnd], o.schmidt(bnd)) < 1e-12
+    # a truncating circuit from |0...0> and U(8) gates
+    n2, chi2 = 14, 24
+    layers2 = C.brickwork(n2, 10, rng, first_u2_layer=True)
+    layers2 += [[(s, C.haar_unitary(8, rng)) for s in range(p, n2 - 2, 3)] for p in (0, 1)]
+    c, _ = _run_eager(n2, chi2, [(4096, bw, SCHED384)], layers2)
+    o2 = oracle.OracleMPS(n2, chi2, 1e-12)
+    for layer in layers2:
+        for s, U in layer:
+            o2.apply_gate(s, U)
+    for bnd in range(n2 - 1):
+        assert spectrum_err(c[2][bnd], o2.schmidt(bnd)) < 1e-12

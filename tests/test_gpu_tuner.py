@@ -20,7 +20,7 @@ def _cuda():
     B.build()
 
 
-@pytest.mark.parametrize("cand", [(16, 2), (8, 2), (16, 0), (8, 0), (16, 1)])
+@pytest.mark.parametrize("cand", [(16, 3), (8, 3), (16, 2), (8, 2), (16, 0), (8, 0), (16, 1)])
 def test_every_candidate_matches_the_oracle(cand):
     from paper_1111_3124_gb300.mps import MPS, PREC_SPLIT
     # a saturated update, theta 128 x 128 cut to 64
@@ -56,7 +56,7 @@ def test_every_candidate_matches_the_oracle(cand):
 def test_tuning_table_rejects_bad_entries():
     from paper_1111_3124_gb300.mps import MPS, MPSError, MPS_ERR_ARG
     m = MPS(4, 8, 0.0)
-    for table in ([(64, 12, 0)], [(64, 8, 1)], [(64, 16, 3)], [(64, 16, -1)], [(128, 16, 0), (64, 16, 0)]):
+    for table in ([(64, 12, 0)], [(64, 8, 1)], [(64, 16, 4)], [(64, 16, -1)], [(128, 16, 0), (64, 16, 0)]):
         with pytest.raises(MPSError) as e:
             m.set_tuning(table)
         assert e.value.code == MPS_ERR_ARG
