@@ -87,7 +87,7 @@ __device__ __forceinline__ void oz_digits(double x, int e, int s, int* d) {
 // mode 0: A operand (row 2r = [Re, -Im], 2r+1 = [Im, Re]);
 // mode 1: B operand (row r = [Re, Im]).
 __global__ void __launch_bounds__(256) k_oz_split(const OzJob* jobs, int which, __nv_bfloat16* out, int* expo,
-                                                  int Mp, int Kp, int s, int k0, int kchunk) {
+                                                  int Mp, int Kp, int s, int k0, int kchunk, int kcap) {
   const OzJob& jb = jobs[blockIdx.y];
   const OzView& v = which == 0 ? jb.a : jb.b;
   const int R = which == 0 ? jb.M : jb.N;
@@ -105,26 +105,35 @@ __global__ void __launch_bounds__(256) k_oz_split(const OzJob* jobs, int which, 
     if (lane == 0) expo[(size_t)blockIdx.y * rows_cap + r] = 0;
     return;
   }
+  // the row is read once, into this warp's part of shared memory (loads
+  // unrolled so that several are in flight), then cut into digits from there
+  extern __shared__ double2 oz_rows[];
+  double2* row = oz_rows + (size_t)warp * kcap;  // K <= kcap
   double mx = 0.0;
+#pragma unroll 4
   for (int k = lane; k < K; k += 32) {
     const double2 x = oz_elem(v, r, k0 + k);
+    row[k] = x;
     mx = fmax(mx, fmax(fabs(x.x), fabs(x.y)));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __syncwarp();
   const int e = oz_exponent(mx);
   if (lane == 0) expo[(size_t)blockIdx.y * rows_cap + r] = e;
   if ((K & 1) == 0) {
     // two consecutive k per lane: every slice row gets 4-byte bf16-pair stores
     // (both halves start at even offsets because K is even)
     for (int k = 2 * lane; k < K; k += 64) {
-      const double2 x0 = oz_elem(v, r, k0 + k), x1 = oz_elem(v, r, k0 + k + 1);
+      const double2 x0 = row[k], x1 = row[k + 1];
       int r0[8], i0[8], r1[8], i1[8];
       oz_digits(x0.x, e, s, r0);
       oz_digits(x0.y, e, s, i0);
       oz_digits(x1.x, e, s, r1);
       oz_digits(x1.y, e, s, i1);
-      for (int p = 0; p < s; ++p) {
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {  // unrolled: the digit arrays stay in registers
+        if (p >= s) break;
         __nv_bfloat162* sl = reinterpret_cast<__nv_bfloat162*>(base + p * slice_stride);
         const __nv_bfloat162 re = __floats2bfloat162_rn((float)r0[p], (float)r1[p]);
         const __nv_bfloat162 im = __floats2bfloat162_rn((float)i0[p], (float)i1[p]);
@@ -142,11 +151,13 @@ __global__ void __launch_bounds__(256) k_oz_split(const OzJob* jobs, int which, 
     }
   } else {
     for (int k = lane; k < K; k += 32) {
-      const double2 x = oz_elem(v, r, k0 + k);
+      const double2 x = row[k];
       int dre[8], dim[8];
       oz_digits(x.x, e, s, dre);
       oz_digits(x.y, e, s, dim);
-      for (int p = 0; p < s; ++p) {
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        if (p >= s) break;
         __nv_bfloat16* sl = base + p * slice_stride;
         if (which == 0) {
           sl[(size_t)(2 * r) * Kp + k] = __float2bfloat16_rn((float)dre[p]);
@@ -397,6 +408,9 @@ int ozaki_prepare() {
   if (done) return 0;
   if (encode_fn()) return -1;
   if (cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem) != cudaSuccess) return -1;
+  if (cudaFuncSetAttribute(k_oz_split, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 512 * (int)sizeof(double2)) !=
+      cudaSuccess)
+    return -1;
   done = true;
   return 0;
 }
@@ -435,8 +449,10 @@ int ozaki_zgemm(const OzJob* d_jobs, int njobs, int M_ub, int N_ub, int K_ub, in
   if (make_map(&mA, Ah, Kp, Mp, s, njobs, kOzM) || make_map(&mB, Bh, Kp, Np, s, njobs, kOzN)) return -3;
   if (ozaki_prepare()) return -4;
   for (int k0 = 0; k0 < K_ub; k0 += kchunk) {
-    k_oz_split<<<dim3((Mp / 2 + 7) / 8, njobs), 256, 0, st>>>(d_jobs, 0, Ah, ea, Mp, Kp, s, k0, kchunk);
-    k_oz_split<<<dim3((Np + 7) / 8, njobs), 256, 0, st>>>(d_jobs, 1, Bh, fb, Np, Kp, s, k0, kchunk);
+    const size_t rows_smem = (size_t)8 * Kc_ub * sizeof(double2);  // one row of K <= Kc_ub per warp
+    k_oz_split<<<dim3((Mp / 2 + 7) / 8, njobs), 256, rows_smem, st>>>(d_jobs, 0, Ah, ea, Mp, Kp, s, k0, kchunk,
+                                                                       Kc_ub);
+    k_oz_split<<<dim3((Np + 7) / 8, njobs), 256, rows_smem, st>>>(d_jobs, 1, Bh, fb, Np, Kp, s, k0, kchunk, Kc_ub);
     k_oz_gemm<<<dim3(Np / kOzN, Mp / kOzM, njobs), kOzThreads, kOzSmem, st>>>(mA, mB, d_jobs, ea, fb, Mp, Np, s, d_err,
                                                                              k0, kchunk);
   }
