@@ -96,9 +96,20 @@ __device__ __forceinline__ Rot make_rot(float al, float be, float2 g, float tiny
   r.tg = 0.f;
   r.on = false;
   if (!(al > tinyf && be > tinyf)) return r;
+  // e with max(al, be) = m 2^e, m in [0.5, 1), and sc = 2^-e: from the bits
+  // for a normal maximum below 2^126 (the same values frexpf and ldexpf give,
+  // in fewer dependent steps), by the library otherwise
+  const float mab = fmaxf(al, be);
+  const bool bits = mab >= 1.17549435e-38f && mab < 8.50705917e+37f;
   int e;
-  frexpf(fmaxf(al, be), &e);
-  const float sc = ldexpf(1.f, -e);  // exact
+  float sc;
+  if (bits) {
+    e = ((__float_as_int(mab) >> 23) & 0xff) - 126;
+    sc = __int_as_float((127 - e) << 23);  // exact
+  } else {
+    frexpf(mab, &e);
+    sc = ldexpf(1.f, -e);  // exact
+  }
   const float a = al * sc, b = be * sc, gx = g.x * sc, gy = g.y * sc;
   const float g2 = fmaf(gx, gx, gy * gy);
   // |g| > eps_32 sqrt(a b)
@@ -109,7 +120,8 @@ __device__ __forceinline__ Rot make_rot(float al, float be, float2 g, float tiny
   const float tx = sg * gx, ty = sg * gy;
   r.c = 1.f / sqrtf(1.f + fmaf(tx, tx, ty * ty));
   r.se = make_float2(r.c * tx, r.c * ty);
-  r.tg = ldexpf(sg * g2, e);  // t |g| in the original scale
+  // t |g| in the original scale (times 2^e: one rounding, as ldexpf)
+  r.tg = bits ? (sg * g2) * __int_as_float((127 + e) << 23) : ldexpf(sg * g2, e);
   return r;
 }
 

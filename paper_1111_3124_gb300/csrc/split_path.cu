@@ -317,14 +317,19 @@ constexpr double kGramXMax = 1e-3;  // larger first-order rotations: left to the
 
 __device__ __forceinline__ bool polishing(const TaskMeta& mt) { return !mt.status && mt.active && !mt.hard; }
 
-// sigma[p] = g_pp (the diagonal, kept while P is overwritten by X)
+// sigma[p] = g_pp (the diagonal, kept while P is overwritten by X), and its
+// square root in V2 (free until X^3 is formed)
 __global__ void k_gram_diag(const GateTask* tasks, TaskMeta* meta) {
   const GateTask& tk = tasks[blockIdx.y];
   TaskMeta& mt = meta[blockIdx.y];
   if (!polishing(mt)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) mt.nhard = 0;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < mt.Nw; p += gridDim.x * blockDim.x)
-    tk.sigma[p] = tk.P[(size_t)p + (size_t)p * mt.Nw].x;
+  double* sq = reinterpret_cast<double*>(tk.V2);  // free until X^3: the square roots k_gram_x needs per pair
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < mt.Nw; p += gridDim.x * blockDim.x) {
+    const double g = tk.P[(size_t)p + (size_t)p * mt.Nw].x;
+    tk.sigma[p] = g;
+    sq[p] = sqrt(g);
+  }
 }
 
 // The binary64 orthogonality test of every pair on G (numerically zero
@@ -337,6 +342,7 @@ __global__ void k_gram_x(const GateTask* tasks, TaskMeta* meta, int form_x) {
   const int nw = mt.Nw;
   const double tol = (double)mt.Mw * kEps64;
   const double tiny = tol * tol * mt.frob2;
+  const double* sq = reinterpret_cast<const double*>(tk.V2);
   int above = 0, hard = 0;
   float mx = 0.f;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)nw * nw;
@@ -348,7 +354,7 @@ __global__ void k_gram_x(const GateTask* tasks, TaskMeta* meta, int form_x) {
       const double2 g = tk.P[e];
       if (app > tiny && aqq > tiny) {
         const double gabs = hypot(g.x, g.y);
-        const double ratio = gabs / (sqrt(app) * sqrt(aqq));
+        const double ratio = gabs / (sq[p] * sq[q]);  // sq = sqrt(sigma), from k_gram_diag
         above |= ratio > tol;
         mx = fmaxf(mx, (float)ratio);
         // the exact Jacobi angle of the pair's 2 x 2 problem, tan 2t =
