@@ -13,7 +13,9 @@
 //      zero columns excluded at binary64 resolution); a pair that passes is
 //      left alone.
 //   3. One cyclic sweep of the two-sided Hermitian Jacobi method on G
-//      (circle-method rounds of 2b/2 disjoint rotations). A round is one
+//      (circle-method rounds of 2b/2 disjoint rotations); after a sweep's
+//      first round of block pairs, only the b rounds of pairs across the two
+//      blocks (the test of step 2 likewise). An inner round is one
 //      barrier: in every warp, lane l forms the rotation of pair l and the
 //      threads take those of their row pair and column pair by shuffle, read
 //      the 2 x 2 block of G those rotations touch, then write J_i^H G_blk J_j
@@ -371,6 +373,12 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
   __syncthreads();
 
   // ---- 2. test (binary64 zero threshold, fp32 resolution)
+  // The first round of a sweep treats every pair of the block pair's columns;
+  // the later rounds only the pairs across the two blocks (each block's own
+  // pairs were treated at the sweep's first round, where every block takes
+  // part once). Every column pair is still tested and rotated at least once a
+  // sweep, so a sweep without a rotation still means every pair passed.
+  const bool cross = round > 0;
   const float tolc = (float)(4.0 * sqrt((double)Mw) * 5.9604644775390625e-08);
   const float tinyf = (float)((double)Mw * 1.1102230246251565e-16 * (double)Mw * 1.1102230246251565e-16 * mt.frob2);
   {
@@ -378,7 +386,7 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
     int nd = 0;
     for (int e = tid; e < C2 * C2; e += NTHR) {
       const int p = e / C2, q = e % C2;
-      if (p >= q) continue;
+      if (p >= q || (cross && (p >= BW || q < BW))) continue;
       const float al = G[p][p].x, be = G[q][q].x;
       if (al > tinyf && be > tinyf) {
         const float ratio = hypotf(G[p][q].x, G[p][q].y) * (rsqrtf(al) * rsqrtf(be));
@@ -407,8 +415,20 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
   const int bi = tid / NP, bj = tid % NP;  // row pair, column pair of this thread's 2 x 2 block
   const int lane = tid & 31;
   const bool blk_warp = (tid & ~31) < NP * NP;  // warps holding 2 x 2 blocks (NP * NP is a multiple of 32)
-  for (int it = 0; it < kF32InnerSweeps * (C2 - 1); ++it) {
-    const int ir = it % (C2 - 1);
+  // the pairs of inner round ir: the circle method over the 2b columns, or
+  // (cross) column l of block I with column (l + ir) mod b of block J
+  const int nround = cross ? BW : C2 - 1;
+  auto inner_pair = [&](int ir, int l, int& P, int& Q) {
+    if (cross) {
+      P = l;
+      Q = BW + (l + ir) % BW;
+    } else {
+      P = prs[ir][l][0];
+      Q = prs[ir][l][1];
+    }
+  };
+  for (int it = 0; it < kF32InnerSweeps * nround; ++it) {
+    const int ir = it % nround;
     auto& Gc = S.G[it & 1];        // this round reads one copy of G ...
     auto& Gn = S.G[(it & 1) ^ 1];  // ... and writes all of the other: one barrier per round
     Rot ri = {1.f, zero, 0.f, false}, rj = ri;
@@ -420,15 +440,14 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
       // of them, then takes its row and column pairs' by shuffle)
       Rot mine = {1.f, zero, 0.f, false};
       if (lane < NP) {
-        const int Pl = prs[ir][lane][0], Ql = prs[ir][lane][1];
+        int Pl, Ql;
+        inner_pair(ir, lane, Pl, Ql);
         mine = make_rot(Gc[Pl][Pl].x, Gc[Ql][Ql].x, Gc[Pl][Ql], tinyf);
       }
       ri = shfl_rot(mine, bi % 32);
       rj = shfl_rot(mine, bj);
-      Pi = prs[ir][bi % NP][0];
-      Qi = prs[ir][bi % NP][1];
-      Pj = prs[ir][bj][0];
-      Qj = prs[ir][bj][1];
+      inner_pair(ir, bi % NP, Pi, Qi);
+      inner_pair(ir, bj, Pj, Qj);
       if (tid < NP * NP) {
         x00 = Gc[Pi][Pj];
         x01 = Gc[Pi][Qj];
