@@ -107,3 +107,23 @@ def test_nominal_work_count():
     assert got["theta"] == sum(t for t, _ in parts) and got["svd"] == sum(v for _, v in parts)
     assert got["total"] == got["theta"] + got["svd"]
     assert stub.calls == ["reset", (2, (0, 2)), (1, (0, 1, 2, 3)), (2, (1,)), "sync"]
+
+
+def test_fp32_launch_mode_lookup():
+    """The roofline names the fp32 sweep kernel and picks its captured traffic
+    from the tuning table as the library applies it: the first entry whose
+    nw_max covers the width, else the last; no table means the library's
+    default (block width 16, scheduled launch of 256-thread CTAs)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    table = [(64, 16, 2), (128, 8, 0), (256, 16, 3), (512, 16, 1)]
+    assert bench.f32_mode(table, 40) == (16, 2)
+    assert bench.f32_mode(table, 128) == (8, 0)
+    assert bench.f32_mode(table, 200) == (16, 3)
+    assert bench.f32_mode(table, 4096) == (16, 1)  # beyond the last entry: the last entry
+    assert bench.f32_mode(None, 512) == (16, 2) and bench.f32_mode([], 512) == (16, 2)
+    assert "k_jacobi_f32_sched<16, 256>" in bench.f32_kernel_name(None, 512)
+    assert "k_jacobi_f32_sched<16, 384>" in bench.f32_kernel_name(table, 200)
+    assert "k_rot_tc" in bench.f32_kernel_name(table, 512)
+    assert "k_jacobi_pair_f32<8>" in bench.f32_kernel_name(table, 100)
+    assert 2 in bench.F32_CAPTURED and 0 in bench.F32_CAPTURED
