@@ -436,16 +436,17 @@ __device__ __forceinline__ void pair_f32(const GateTask* tasks, TaskMeta* meta, 
     float2 x00 = zero, x01 = zero, x10 = zero, x11 = zero;
     float2 w[2][2] = {{zero, zero}, {zero, zero}};
     if (blk_warp) {  // warp-uniform
-      // lane l < NP forms the rotation of pair l (every block warp forms all
-      // of them, then takes its row and column pairs' by shuffle)
-      Rot mine = {1.f, zero, 0.f, false};
-      if (lane < NP) {
+      // lane l forms the rotation of pair l mod NP (every block warp forms all
+      // of them): that is this thread's column pair bj, and its row pair's
+      // comes from lane bi by shuffle
+      Rot mine;
+      {
         int Pl, Ql;
-        inner_pair(ir, lane, Pl, Ql);
+        inner_pair(ir, lane % NP, Pl, Ql);
         mine = make_rot(Gc[Pl][Pl].x, Gc[Ql][Ql].x, Gc[Pl][Ql], tinyf);
       }
       ri = shfl_rot(mine, bi % 32);
-      rj = shfl_rot(mine, bj);
+      rj = mine;
       inner_pair(ir, bi % NP, Pi, Qi);
       inner_pair(ir, bj, Pj, Qj);
       if (tid < NP * NP) {
