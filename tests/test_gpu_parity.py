@@ -174,6 +174,34 @@ def test_chi_max_one_closed_form():
     assert abs(abs(g.amplitude([0, 0])) - 1) < 1e-14
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_degenerate_cut_keeps_a_valid_state(prec):
+    """The oracle's tie pin on the GPU, in both modes: a Bell state cut to
+    chi_max = 1. Its two Schmidt values tie, so either branch is a valid
+    truncation; what is unique is compared: one kept value, discarded weight
+    1/2, Lambda = [1], and a state that is one of the two branches. A larger
+    case ties in the middle of the spectrum: GHZ on 6 qubits cut to chi_max = 1
+    after the entangling prefix."""
+    g = gpu_mps(2, 1, 0.0, prec)
+    g.apply_gate(0, np.kron(C.H, C.I2))
+    g.apply_gate(0, C.CNOT)
+    d = g.diag()
+    assert d["k"][0] == 1 and abs(d["discarded"][0] - 0.5) < 1e-14
+    np.testing.assert_allclose(g.schmidt(0), [1.0], atol=1e-14)
+    a = np.abs(g.amplitudes(np.array([[0, 0], [0, 1], [1, 0], [1, 1]], dtype=np.uint8)))
+    assert abs(max(a[0], a[3]) - 1) < 1e-14 and min(a[0], a[3]) < 1e-15 and max(a[1], a[2]) < 1e-15
+    n = 6
+    h = gpu_mps(n, 1, 0.0, prec)
+    for layer in C.ghz_prefix(n):
+        for site, U in layer:
+            h.apply_gate(site, U)
+    for b in range(n - 1):
+        np.testing.assert_allclose(h.schmidt(b), [1.0], atol=1e-14)
+    amps = np.abs(h.amplitudes(all_bits(n)))
+    assert abs(np.max(amps) - 1) < 1e-13 and np.sum(amps > 1e-13) == 1
+    assert amps[np.argmax(amps)] == max(amps[0], amps[-1])  # a GHZ branch: all zeros or all ones
+
+
 # --------------------------------------------- single updates, teacher forced ---
 
 def single_update(chi, chi_max, site, d, seed, cutoff=1e-12):
