@@ -601,31 +601,38 @@ __global__ void __launch_bounds__(256, 3)
 // ---- Scheduled sweeps: every fp32 sweep of every task in one launch
 //
 // The work items (sweep s, round r, task t, pair p) are numbered sweep-major,
-// then by round, task and pair. A CTA takes the next number from a counter,
-// waits until the item's inputs are final, runs the pair (steps 1-4) and
-// reports it. An item depends on the two items of the previous round of its
-// own task that last wrote its blocks I and J, and, in the first round of a
-// sweep, on the decision taken at the end of the task's previous sweep. The
-// dependency on A and on V is tracked apart (per-block round counters of
-// each, qver): a pair releases A_I, A_J as soon as it has rotated them, so
-// the next round's Gram can start while it rotates V_I, V_J, which it does
-// once the previous round has finished with them. The
-// numbering is a topological order of these dependencies and a CTA takes an
-// item only while it runs, so the unfinished item with the smallest number
-// always has its inputs ready and every wait ends. Each wait is bounded all
-// the same (kSchedWaitNs by %globaltimer): one that runs out sets the error
-// word and every CTA of the launch returns.
+// then by round, task and pair. A CTA takes the next number from a counter
+// (the number after that already while it runs the current item), waits until
+// the item's inputs are final, runs the pair (steps 1-4) and reports it.
+//
+// An item depends on the two items of the previous round of its own task that
+// last wrote its blocks I and J, and, in the first round of a sweep, on the
+// decision taken at the end of the task's previous sweep. The dependency on A
+// and on V is tracked apart (per-block round counters of each, qver): a pair
+// releases A_I, A_J as soon as it has rotated them, so the next round's Gram
+// can start while it rotates V_I, V_J, which it does once the previous round
+// has finished with them.
+//
+// The numbering is a topological order of these dependencies, and a CTA
+// takes numbers only while it runs and runs its items in the order taken. So
+// the unfinished item with the smallest number always has its inputs final
+// and every wait ends. Each wait is bounded all the same (kSchedWaitNs by
+// %globaltimer): one that runs out sets the error word and every CTA of the
+// launch returns.
 //
 // Per task, q_done counts the finished pairs of all its sweeps. The CTA that
 // finishes the last pair of a sweep takes the end-of-sweep decision (the task
 // stops when no pair rotated, or at the sweep limit) and then publishes it in
 // q_sweep: the next sweep's number, or kSweepStopped, which ends the wait of
 // any later item of the task (such items are skipped). Tasks that do not
-// sweep at all start at kSweepStopped. Each task runs the pairs, rounds and sweeps of the per-round
-// launches on the same data, so the results are the same bit for bit; only
-// the order in which independent pairs run differs. What this removes is the
-// launch per round and the partly filled last wave of every round (a
-// saturated round of 32 tasks is 512 CTAs against 456 resident).
+// sweep at all start at kSweepStopped.
+//
+// Each task runs the pairs, rounds and sweeps of the per-round launches on the
+// same data, so the results are the same bit for bit; only the order in which
+// independent pairs run differs. What this removes is the launch per round and
+// the partly filled last wave of every round (a saturated round of 32 tasks is
+// 512 CTAs against 456 resident); and a task's next round no longer waits for
+// the slowest pair of every other task's round.
 struct F32Sched {
   unsigned long long head;  // next work item
   int n_active;             // tasks still sweeping
